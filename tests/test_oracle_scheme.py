@@ -1,0 +1,337 @@
+"""Pins of the oracle's whole pseudo-time iteration (Sec 2.2-2.4) against invariants, exact symmetries,
+an independent dense linear solve and a brute-force time-domain run.
+
+None of the expected values comes from the oracle's own arithmetic: each test states a property the
+paper or the mathematics fixes and checks the oracle against it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2605_03479_gb300 import inputs as I
+
+
+def run(case, niter, seed=None, amp=0.01, **kw):
+    P = O.Problem(case, **kw)
+    W, h, b = I.initial_state(case, seed=seed, amp=amp)
+    res = O.iterate(P, W, h, b, niter)
+    return P, W, h, b, res
+
+
+# ------------------------------------------------------------------ rest state (Sec 2.2 - 2.4)
+
+@pytest.mark.parametrize("nh,kn,st,pr", [(1, 0.1, 1.0, 1.0), (2, 0.01, 10.0, 2 / 3), (3, 5.0, 0.3, 2 / 3)])
+def test_rest_state_is_a_fixed_point(nh, kn, st, pr):
+    """Uniform Maxwellian, resting walls at T0: slopes, a, A and q vanish, C1 + C4 = dG, E.const = 0 and the
+    symmetric grid gives rho_w = rho_0, so W and h do not move (velocity grid wide enough that its
+    quadrature of the Maxwellian is exact to round-off)."""
+    c = I.make_case("rest", 5, 32, kn=kn, st=st, nh=nh, pr=pr, drive="rest", half_width=6.5, stretched_ratio=1.1)
+    P = O.Problem(c)
+    W, h, b = I.initial_state(c)
+    W0, h0, b0 = W.copy(), h.copy(), b.copy()
+    res = O.iterate(P, W, h, b, 3)
+    assert np.max(res) < 1e-14
+    assert np.max(np.abs(W - W0)) < 1e-14
+    assert np.max(np.abs(h - h0)) < 1e-14 * np.max(h0)
+    assert np.max(np.abs(b - b0)) < 1e-14 * np.max(b0)
+
+
+# ------------------------------------------------------------------ conservation (Eq. fv_W)
+
+def test_mass_conservation_with_local_steps():
+    """Interior face fluxes cancel pairwise, the wall mass flux is zero by Eq. rho_wall and E has zero column
+    sums, so sum_{i,n} |Omega_i| (rho^{k+1} - rho^k) / dG_i = 0 to round-off."""
+    c = I.tiny_case(ncell=7, nvel=10, kn=0.3, st=2.0, nh=2, pr=2 / 3, drive="thermal", amp=0.4,
+                    stretched_ratio=1.1)
+    P = O.Problem(c)
+    W, h, b = I.initial_state(c, seed=7)
+    area = np.outer(np.diff(c.ynodes), np.diff(c.xnodes)).reshape(-1)
+    for _ in range(4):
+        dG = O.cell_steps(P, W)
+        rho0 = W[:, :, 0].copy()
+        O.iterate(P, W, h, b, 1)
+        drift = np.sum(area[None, :] * (W[:, :, 0] - rho0) / dG[None, :])
+        scale = np.sum(area[None, :] * W[:, :, 0] / dG[None, :])
+        assert abs(drift) < 1e-14 * scale
+
+
+def test_mass_conservation_with_a_global_step():
+    c = I.tiny_case(ncell=6, nvel=10, kn=0.05, st=1.0, nh=1, pr=2 / 3, drive="shear", amp=0.05)
+    P, W, h, b, _ = run(c, 0, seed=3)
+    P = O.Problem(c, dt_fixed=2e-3)
+    area = np.outer(np.diff(c.ynodes), np.diff(c.xnodes)).reshape(-1)
+    m0 = np.sum(area[None, :] * W[:, :, 0])
+    O.iterate(P, W, h, b, 10)
+    assert abs(np.sum(area[None, :] * W[:, :, 0]) - m0) < 1e-14 * m0
+
+
+# ------------------------------------------------------------------ time-independent drive
+
+def test_time_independent_drive_keeps_levels_identical_and_matches_other_nt():
+    """A steady lid (U_hat = 0) with identical initial levels: every level stays identical, and level 0 does
+    not depend on N_T when omega N_H (the spectral radius in Eq. dt_hb) is the same."""
+    def case(nh, st):
+        c = I.tiny_case(ncell=6, nvel=10, kn=0.2, st=st, nh=nh, pr=2 / 3, drive="rest")
+        c.walls[I.TOP][0] = 0.02          # mean lid velocity
+        return c
+    cA, cB = case(1, 2.0), case(2, 1.0)
+    PA, PB = O.Problem(cA), O.Problem(cB)
+    WA, hA, bA = I.initial_state(cA)
+    WB, hB, bB = I.initial_state(cB)
+    for _ in range(6):
+        O.iterate(PA, WA, hA, bA, 1)
+        O.iterate(PB, WB, hB, bB, 1)
+        for n in range(1, 5):
+            np.testing.assert_allclose(hB[n], hB[0], rtol=0, atol=1e-14 * hB.max())
+        np.testing.assert_allclose(hA[1], hA[0], rtol=0, atol=1e-14 * hA.max())
+        np.testing.assert_allclose(WA[0], WB[0], rtol=1e-13, atol=1e-15)
+        np.testing.assert_allclose(hA[0], hB[0], rtol=0, atol=1e-14 * hA.max())
+
+
+# ------------------------------------------------------------------ exact symmetries
+
+def _mirror_x(case, W, h, b):
+    nx, ny, nu, nv = case.nx, case.ny, case.nu, case.nv
+    nt = W.shape[0]
+    W = W.reshape(nt, ny, nx, 4)[:, :, ::-1, :].copy()
+    W[..., 1] *= -1.0
+    h = h.reshape(nt, ny, nx, nv, nu)[:, :, ::-1, :, ::-1]
+    b = b.reshape(nt, ny, nx, nv, nu)[:, :, ::-1, :, ::-1]
+    return (np.ascontiguousarray(W.reshape(nt, -1, 4)), np.ascontiguousarray(h.reshape(nt, nx * ny, -1)),
+            np.ascontiguousarray(b.reshape(nt, nx * ny, -1)))
+
+
+def _transpose(case, W, h, b):
+    nx, ny, nu, nv = case.nx, case.ny, case.nu, case.nv
+    nt = W.shape[0]
+    W = W.reshape(nt, ny, nx, 4).transpose(0, 2, 1, 3)[..., [0, 2, 1, 3]]
+    h = h.reshape(nt, ny, nx, nv, nu).transpose(0, 2, 1, 4, 3)
+    b = b.reshape(nt, ny, nx, nv, nu).transpose(0, 2, 1, 4, 3)
+    return (np.ascontiguousarray(W.reshape(nt, -1, 4)), np.ascontiguousarray(h.reshape(nt, nx * ny, -1)),
+            np.ascontiguousarray(b.reshape(nt, nx * ny, -1)))
+
+
+def test_mirror_symmetry_of_the_shear_cavity():
+    """Reversing the lid velocity is the mirror image x -> 1 - x (with u -> -u): exact on a symmetric mesh
+    and velocity grid, iteration by iteration."""
+    cA = I.tiny_case(ncell=6, nvel=10, kn=0.1, st=1.5, nh=1, pr=2 / 3, drive="shear", amp=0.02,
+                     stretched_ratio=1.1)
+    cB = I.tiny_case(ncell=6, nvel=10, kn=0.1, st=1.5, nh=1, pr=2 / 3, drive="shear", amp=-0.02,
+                     stretched_ratio=1.1)
+    WA, hA, bA = I.initial_state(cA, seed=11)
+    WB, hB, bB = _mirror_x(cA, WA, hA, bA)
+    PA, PB = O.Problem(cA), O.Problem(cB)
+    O.iterate(PA, WA, hA, bA, 8)
+    O.iterate(PB, WB, hB, bB, 8)
+    Wm, hm, bm = _mirror_x(cA, WA, hA, bA)
+    np.testing.assert_allclose(WB, Wm, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(hB, hm, rtol=0, atol=1e-13 * hA.max())
+    np.testing.assert_allclose(bB, bm, rtol=0, atol=1e-13 * bA.max())
+
+
+def test_transpose_symmetry_exchanges_axes():
+    """A top lid moving in +x is the transpose (x <-> y, u <-> v) of a right wall moving in +y, and a heated
+    bottom wall the transpose of a heated left wall: checks that the two face orientations agree."""
+    cA = I.tiny_case(ncell=6, nvel=10, kn=0.2, st=1.0, nh=1, pr=2 / 3, drive="shear", amp=0.03)
+    cA.walls[I.BOTTOM][8] = -0.2
+    cB = I.tiny_case(ncell=6, nvel=10, kn=0.2, st=1.0, nh=1, pr=2 / 3, drive="rest")
+    cB.walls[I.RIGHT][5] = 0.03          # V_re on the right wall
+    cB.walls[I.LEFT][8] = -0.2
+    WA, hA, bA = I.initial_state(cA, seed=5)
+    WB, hB, bB = _transpose(cA, WA, hA, bA)
+    PA, PB = O.Problem(cA), O.Problem(cB)
+    O.iterate(PA, WA, hA, bA, 8)
+    O.iterate(PB, WB, hB, bB, 8)
+    Wt, ht, bt = _transpose(cA, WA, hA, bA)
+    np.testing.assert_allclose(WB, Wt, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(hB, ht, rtol=0, atol=1e-13 * hA.max())
+    np.testing.assert_allclose(bB, bt, rtol=0, atol=1e-13 * bA.max())
+
+
+# ------------------------------------------------------------------ dense linear solve (first order, free molecular)
+
+def _first_order_matrix(case):
+    """Eqs. hb_micro_h, fv_h, bc_diffuse and rho_wall in the free-molecular limit with zero slopes: per level n,
+    cell i, velocity a: (1/|Omega_i|) sum_f |L_f| s_f u_n h_upwind + omega sum_m E_nm h_m = 0, where a wall
+    face carries the interior h for incident velocities and rho_w H_w for reflected ones, rho_w linear in h."""
+    nx, ny, nu, nv, nt = case.nx, case.ny, case.nu, case.nv, case.nt
+    nc, na = nx * ny, nu * nv
+    N = nt * nc * na
+    M = np.zeros((N, N))
+    idx = lambda n, c, a: (n * nc + c) * na + a
+    dx, dy = np.diff(case.xnodes), np.diff(case.ynodes)
+    uu = np.tile(case.u, nv)
+    vv = np.repeat(case.v, nu)
+    ww = np.outer(case.wv, case.wu).reshape(-1)
+    om = O.omega_from_st(case.st)
+    th = 2 * math.pi * np.arange(nt) / nt
+    E = np.zeros((nt, nt))
+    for n in range(nt):
+        for m in range(nt):
+            if n != m:
+                E[n, m] = 0.5 * (-1) ** (n - m) / math.sin(math.pi * (n - m) / nt)
+
+    def wall_maxwell(wall, n):
+        p = case.walls[wall]
+        Uw = p[0] + p[3] * math.cos(th[n]) - p[4] * math.sin(th[n])
+        Vw = p[1] + p[5] * math.cos(th[n]) - p[6] * math.sin(th[n])
+        Tw = p[2] + p[7] * math.cos(th[n]) - p[8] * math.sin(th[n])
+        lam = 1.0 / Tw
+        return lam / math.pi * np.exp(-lam * ((uu - Uw) ** 2 + (vv - Vw) ** 2))
+
+    for n in range(nt):
+        for j in range(ny):
+            for i in range(nx):
+                c = j * nx + i
+                area = dx[i] * dy[j]
+                for a in range(na):
+                    r = idx(n, c, a)
+                    for m in range(nt):
+                        M[r, idx(m, c, a)] += om * E[n, m]
+                # faces: (axis, side s = outward sign, neighbour cell or wall id, length)
+                faces = [(0, -1, (j * nx + i - 1) if i > 0 else ("w", 3), dy[j]),
+                         (0, +1, (j * nx + i + 1) if i < nx - 1 else ("w", 1), dy[j]),
+                         (1, -1, ((j - 1) * nx + i) if j > 0 else ("w", 0), dx[i]),
+                         (1, +1, ((j + 1) * nx + i) if j < ny - 1 else ("w", 2), dx[i])]
+                for axis, s, nb, length in faces:
+                    un = uu if axis == 0 else vv
+                    coef = s * length / area
+                    if isinstance(nb, tuple):
+                        Hw = wall_maxwell(nb[1], n)
+                        inc = (un * s > 0)        # moving out of the cell, into the wall
+                        ref = (un * s < 0)
+                        den = np.sum(ww[ref] * np.abs(un[ref]) * Hw[ref])
+                        for a in range(na):
+                            r = idx(n, c, a)
+                            if inc[a]:
+                                M[r, idx(n, c, a)] += coef * un[a]
+                            elif ref[a]:
+                                # un * rho_w Hw, rho_w = sum_inc w |u_n| h / den
+                                for a2 in np.nonzero(inc)[0]:
+                                    M[r, idx(n, c, a2)] += coef * un[a] * Hw[a] * ww[a2] * abs(un[a2]) / den
+                    else:
+                        for a in range(na):
+                            r = idx(n, c, a)
+                            up = c if un[a] * s > 0 else nb   # upwind cell
+                            M[r, idx(n, up, a)] += coef * un[a]
+    return M
+
+
+@pytest.mark.slow
+def test_first_order_free_molecular_fixed_point_solves_the_linear_system():
+    c = I.tiny_case(ncell=4, nvel=8, kn=1e9, st=0.7, nh=1, pr=1.0, drive="shear", amp=0.05)
+    c.walls[I.BOTTOM][8] = -0.2
+    W, h, b = I.initial_state(c)
+    # one global step: with local steps the undamped level-mass harmonics (pure rotation under omega E)
+    # pick up the transient and keep the iterate off the fixed point; the fixed point itself is the same
+    P = O.Problem(c, first_order=True, dt_fixed=float(O.cell_steps(O.Problem(c), W).min()))
+    for _ in range(100):
+        hprev = h.copy()
+        O.iterate(P, W, h, b, 200)
+        if np.max(np.abs(h - hprev)) < 1e-14 * np.max(h):
+            break
+    M = _first_order_matrix(c)
+    # the system is homogeneous (diffuse walls conserve mass): replace one row by a mass normalisation
+    nc, na = c.nc, c.nvel
+    area = np.outer(np.diff(c.ynodes), np.diff(c.xnodes)).reshape(-1)
+    ww = np.outer(c.wv, c.wu).reshape(-1)
+    mass_row = (np.ones(c.nt)[:, None, None] * area[None, :, None] * ww[None, None, :]).reshape(-1)
+    A = M.copy()
+    A[0] = mass_row
+    rhs = np.zeros(A.shape[0])
+    rhs[0] = mass_row @ h.reshape(-1)
+    hs = np.linalg.solve(A, rhs)
+    assert np.max(np.abs(M @ h.reshape(-1))) < 1e-9 * np.max(np.abs(M) @ np.abs(h.reshape(-1)))
+    np.testing.assert_allclose(h.reshape(-1), hs, rtol=0, atol=1e-9 * np.max(hs))
+
+
+# ------------------------------------------------------------------ linear response (small amplitude)
+
+def _converge(case, tol=1e-12, maxit=20000, seed=None):
+    """Iterate to residual `tol` with one global pseudo-time step (the smallest local one): the HB fixed point
+    does not depend on the step, and a global step keeps the per-level mass exactly conserved."""
+    W, h, b = I.initial_state(case, seed=seed)
+    P = O.Problem(case, dt_fixed=float(O.cell_steps(O.Problem(case), W).min()))
+    it = 0
+    while it < maxit:
+        res = O.iterate(P, W, h, b, 200)
+        it += 200
+        if res[-1, 0] < tol:
+            break
+    assert res[-1, 0] < tol, res[-1]
+    return P, W, h, b
+
+
+def _amplitude_series(nh, first_order):
+    """(U_hat_1 / U_a, rho_hat_0 - rho_hat_0(U_a = 0)) for U_a = 0.0025, 0.005, 0.01 at convergence."""
+    out, base = [], None
+    for ua in (0.0, 0.0025, 0.005, 0.01):
+        c = I.tiny_case(ncell=5, nvel=8, kn=0.5, st=1.0, nh=nh, pr=1.0, drive="shear", amp=ua)
+        W, h, b = I.initial_state(c)
+        P = O.Problem(c, first_order=first_order, dt_fixed=float(O.cell_steps(O.Problem(c), W).min()))
+        for _ in range(100):
+            if O.iterate(P, W, h, b, 200)[-1, 0] < 1e-14:
+                break
+        H = O.harmonics(np.stack([O.fields(P, h, b, n) for n in range(c.nt)]))
+        if ua == 0.0:
+            base = H
+            continue
+        out.append((H[1, 1] / ua, H[0, 0] - base[0, 0]))
+    return out
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("nh,ratio", [(1, 2.0), (2, 4.0)])
+def test_response_scaling_with_amplitude_first_order(nh, ratio):
+    """Small-amplitude shear drive with the (analytic) first-order reconstruction: U_hat_1 / U_a tends to a
+    limit whose correction comes from the quadratic nonlinearity.  Its second harmonic aliases onto harmonic -1
+    when N_T = 3 (Sec 2.2 collocation), so the correction is linear in U_a for N_H = 1 (ratio 2 per doubling)
+    and quadratic once N_H = 2 resolves that harmonic (ratio 4).  The mean density change is quadratic."""
+    out = _amplitude_series(nh, True)
+    d1 = np.max(np.abs(out[1][0] - out[0][0]))
+    d2 = np.max(np.abs(out[2][0] - out[1][0]))
+    assert abs(d2 / d1 - ratio) < 0.05 * ratio, (d1, d2)
+    assert d2 < 1e-3 * np.max(np.abs(out[0][0]))
+    r = np.max(np.abs(out[2][1])) / np.max(np.abs(out[1][1]))
+    assert abs(r - 4.0) < 0.05
+
+
+@pytest.mark.slow
+def test_response_is_linear_with_limiter():
+    """With the van Leer reconstruction the scheme is not analytic in U_a, but the response stays linear:
+    U_hat_1 / U_a changes by less than 1e-4 relative between U_a = 0.005 and 0.01 (N_H = 2)."""
+    out = _amplitude_series(2, False)
+    assert np.max(np.abs(out[2][0] - out[1][0])) < 1e-4 * np.max(np.abs(out[0][0]))
+
+
+# ------------------------------------------------------------------ brute force: explicit time domain
+
+@pytest.mark.slow
+def test_harmonic_balance_matches_time_marching():
+    """The converged HB levels equal the periodic state of explicit time-domain UGKS (same flux and walls,
+    E replaced by physical time marching) sampled at t_n, to discretisation error that shrinks with the step
+    (the paper reports < 0.3 % between the two, Sec 3.2.4)."""
+    c = I.tiny_case(ncell=4, nvel=8, kn=1.0, st=1.0, nh=1, pr=1.0, drive="shear", amp=0.01, cfl=0.4)
+    P, W, h, b = _converge(c, tol=1e-13)
+    Hhb = O.harmonics(np.stack([O.fields(P, h, b, n) for n in range(3)]))
+    errs = []
+    period = 2 * math.pi / O.omega_from_st(c.st)
+    for steps_per_level in (120, 240):
+        nsub = 3 * steps_per_level
+        dt = period / nsub
+        ctd = I.tiny_case(ncell=4, nvel=8, kn=1.0, st=1.0, nh=0, pr=1.0, drive="shear", amp=0.01)
+        Wt, ht, bt = I.initial_state(ctd)
+        samples = []
+        for p in range(40):
+            samples = []
+            for s in range(nsub):
+                if s % steps_per_level == 0:
+                    samples.append(O.fields(O.Problem(ctd), ht, bt, 0))
+                Pt = O.Problem(ctd, theta0=2 * math.pi * (s + 0.5) / nsub, dt_fixed=dt)
+                O.iterate(Pt, Wt, ht, bt, 1)
+        Htd = O.harmonics(np.stack(samples))
+        errs.append(np.max(np.abs(Htd[1, 1] - Hhb[1, 1])) / np.max(np.abs(Hhb[1, 1])))
+    assert errs[0] < 0.03, errs
+    assert errs[1] < errs[0], errs
