@@ -1,0 +1,734 @@
+// C ABI of the GB300 HB-UGKS library (declared in include/hbugks.h): workspace layout, case tables, graph
+// capture of the pseudo-time iteration, state and field conversions.  All device memory lives in the
+// caller's workspace; the library allocates none.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "hbugks.h"
+#include "hb_kernels.cuh"
+
+using namespace hb;
+
+namespace {
+
+#define HB_CK(x)                                             \
+    do {                                                     \
+        cudaError_t e_ = (x);                                \
+        if (e_ != cudaSuccess) {                             \
+            last_cuda_error() = e_;                          \
+            return HBUGKS_ECUDA;                             \
+        }                                                    \
+    } while (0)
+
+cudaError_t& last_cuda_error()
+{
+    static thread_local cudaError_t e = cudaSuccess;
+    return e;
+}
+
+constexpr int CHUNK = 16;   // iterations per captured graph
+
+// bump allocator over the workspace; with base == nullptr it only measures
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <class X>
+    X* take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        X* p = base ? reinterpret_cast<X*>(base + off) : nullptr;
+        off += count * sizeof(X);
+        return p;
+    }
+};
+
+struct HostCase {
+    hbugks_case src;
+    int nx, ny, nu, nv, nvel, nvb, nvp, nt, nh, nfx, nf, nc;
+    std::vector<double> xn, yn, u, wu, v, wv;
+    double mu0, omega;
+    std::vector<double> wall_tab;   // [4][nt][3]
+    int k1b, k2b, k3b, k4b, ksb;
+};
+
+bool validate(const hbugks_case& c)
+{
+    const hbugks_mesh& m = c.mesh;
+    const hbugks_vgrid& g = c.vgrid;
+    const hbugks_physics& p = c.phys;
+    if (m.nx < 1 || m.ny < 1 || !m.xnodes || !m.ynodes) return false;
+    if (g.nu < 1 || g.nv < 1 || !g.u || !g.v || !g.wu || !g.wv) return false;
+    if (p.n_harmonics < 0 || 2 * p.n_harmonics + 1 > MAXNT) return false;
+    if (!(p.kn > 0) || !(p.cfl > 0) || !(p.st >= 0) || !(p.gamma > 0)) return false;
+    if (p.precision != 0 && p.precision != 1) return false;
+    if (p.face_step != 0 && p.face_step != 1) return false;
+    for (int i = 0; i < m.nx; ++i) if (!(m.xnodes[i + 1] > m.xnodes[i])) return false;
+    for (int j = 0; j < m.ny; ++j) if (!(m.ynodes[j + 1] > m.ynodes[j])) return false;
+    for (int i = 0; i < g.nu; ++i) if (!(g.wu[i] > 0)) return false;
+    for (int j = 0; j < g.nv; ++j) if (!(g.wv[j] > 0)) return false;
+    for (int w = 0; w < 4; ++w) {
+        const hbugks_wall& wl = c.walls[w];
+        for (int n = 0; n < 2 * p.n_harmonics + 1; ++n) {
+            double th = 2.0 * M_PI * n / (2 * p.n_harmonics + 1);
+            if (!(wl.T_mean + wl.T_re * cos(th) - wl.T_im * sin(th) > 0)) return false;
+        }
+    }
+    return true;
+}
+
+void fill_host(HostCase& h, const hbugks_case& c)
+{
+    h.src = c;
+    h.nx = c.mesh.nx; h.ny = c.mesh.ny; h.nu = c.vgrid.nu; h.nv = c.vgrid.nv;
+    h.nvel = h.nu * h.nv;
+    h.nvb = (h.nvel + VB - 1) / VB;
+    h.nvp = h.nvb * VB;
+    h.nh = c.phys.n_harmonics;
+    h.nt = 2 * h.nh + 1;
+    h.nfx = h.ny * (h.nx + 1);
+    h.nf = h.nfx + (h.ny + 1) * h.nx;
+    h.nc = h.nx * h.ny;
+    h.xn.assign(c.mesh.xnodes, c.mesh.xnodes + h.nx + 1);
+    h.yn.assign(c.mesh.ynodes, c.mesh.ynodes + h.ny + 1);
+    h.u.assign(c.vgrid.u, c.vgrid.u + h.nu);
+    h.wu.assign(c.vgrid.wu, c.vgrid.wu + h.nu);
+    h.v.assign(c.vgrid.v, c.vgrid.v + h.nv);
+    h.wv.assign(c.vgrid.wv, c.vgrid.wv + h.nv);
+    // Eq. def_Kn with H = rho0 = 1, sqrt(2 R T0) = 1:  mu(T0) = Kn sqrt(pi) / F(alpha, w)
+    const double a = c.phys.alpha_vss, w = c.phys.w_vss;
+    const double F = 4.0 * a * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (a + 1.0) * (a + 2.0));
+    h.mu0 = c.phys.kn * sqrt(M_PI) / F;
+    h.omega = c.phys.st;   // Eq. def_St with H = 1, sqrt(2 R T0) = 1
+    h.wall_tab.assign(4 * h.nt * 3, 0.0);
+    for (int wl = 0; wl < 4; ++wl)
+        for (int n = 0; n < h.nt; ++n) {
+            const hbugks_wall& W = h.src.walls[wl];
+            double th = 2.0 * M_PI * n / h.nt;
+            double cs = cos(th), sn = sin(th);
+            double* o = &h.wall_tab[(wl * h.nt + n) * 3];
+            o[0] = W.u_mean + W.u_re * cs - W.u_im * sn;   // Eq. bc_vel
+            o[1] = W.v_mean + W.v_re * cs - W.v_im * sn;
+            o[2] = W.T_mean + W.T_re * cs - W.T_im * sn;   // Eq. bc_temp
+        }
+    h.k1b = ((h.nf + h.nc) * h.nt + 7) / 8;
+    h.k2b = (h.nf * h.nt + 127) / 128;
+    h.k3b = (h.nc + K3_THREADS - 1) / K3_THREADS;
+    h.k4b = (h.nc * h.nvb + 7) / 8;
+    h.ksb = (h.nc + 127) / 128;
+}
+
+template <typename T>
+void layout_case(Carver& cv, const HostCase& h, CaseDev<T>& d)
+{
+    d.nx = h.nx; d.ny = h.ny; d.nu = h.nu; d.nv = h.nv; d.nvel = h.nvel; d.nvb = h.nvb;
+    d.nt = h.nt; d.nh = h.nh; d.nfx = h.nfx; d.nf = h.nf; d.nc = h.nc;
+    d.face_step = h.src.phys.face_step;
+    d.omega = h.omega; d.mu0 = h.mu0; d.w_vss = h.src.phys.w_vss; d.pr = h.src.phys.pr;
+    d.cfl = h.src.phys.cfl; d.gam = h.src.phys.gamma; d.umax = h.src.vgrid.umax; d.vmax = h.src.vgrid.vmax;
+    d.lam0 = 1.0;
+    for (int k = 0; k < 8; ++k) d.e[k] = 0.0;
+    for (int dd = 1; dd <= h.nh; ++dd) d.e[dd] = ((dd & 1) ? -0.5 : 0.5) / sin(M_PI * dd / h.nt);   // Eq. D_explicit
+    d.wall = cv.take<double>(4 * h.nt * 3);
+    d.xn = cv.take<double>(h.nx + 1); d.yn = cv.take<double>(h.ny + 1);
+    d.xc = cv.take<double>(h.nx); d.yc = cv.take<double>(h.ny);
+    d.hx = cv.take<double>(h.nx); d.hy = cv.take<double>(h.ny);
+    d.rdx = cv.take<double>(h.nx); d.rdy = cv.take<double>(h.ny);
+    d.vu = cv.take<double>(h.nvp); d.vv = cv.take<double>(h.nvp); d.vw = cv.take<double>(h.nvp);
+    d.tu = cv.take<T>(h.nvp); d.tv = cv.take<T>(h.nvp); d.tw = cv.take<T>(h.nvp); d.thref = cv.take<T>(h.nvp);
+    d.u1 = cv.take<double>(h.nu); d.wu1 = cv.take<double>(h.nu);
+    d.v1 = cv.take<double>(h.nv); d.wv1 = cv.take<double>(h.nv);
+    d.refmom = cv.take<double>(5 * 13);
+    const size_t ns = (size_t)h.nvb * h.nc * h.nt * VB;
+    for (int k = 0; k < 2; ++k) {
+        d.dh[k] = cv.take<T>(ns);
+        d.db[k] = cv.take<T>(ns);
+        d.W[k] = cv.take<double>((size_t)h.nt * h.nc * 4);
+    }
+    d.dG = cv.take<double>(h.nc);
+    d.fmom = cv.take<double>((size_t)h.nf * h.nt * NM);
+    d.cmom = cv.take<double>((size_t)h.nc * h.nt * NCM);
+    d.fpar = cv.take<T>((size_t)h.nf * h.nt * NP);
+    d.fflux = cv.take<double>((size_t)h.nf * h.nt * 4);
+    d.cpar = cv.take<T>((size_t)h.nc * h.nt * NCP);
+    d.rpart = cv.take<double>((size_t)h.k3b * 4);
+    d.rhist = cv.take<double>((size_t)RING * 4);
+    size_t stage = std::max((size_t)h.nc * h.nvp, (size_t)(h.nt * 8 + 16) * h.nc);
+    d.stage = cv.take<double>(stage);
+}
+
+}  // namespace
+
+// ====================================================================================== solver
+
+struct SolverBase {
+    virtual ~SolverBase() {}
+};
+
+template <typename T>
+struct Impl {
+    std::vector<HostCase> hc;
+    std::vector<CaseDev<T>> dc;
+    CaseDev<T>* d_cases = nullptr;
+    CaseStatus* d_status = nullptr;
+    double* d_tol = nullptr;
+    int* d_off = nullptr;            // [kernel][ncases + 1]
+    std::vector<int> off_host;
+    std::vector<int> nt_groups;      // distinct N_T values
+    int n_off_tables = 0;
+    int tot[5] = {0, 0, 0, 0, 0};    // total blocks of k1, k2, k3, ksteps per batch
+    std::vector<int> k4tot;          // per N_T group
+};
+
+struct hbugks_solver {
+    int ncases = 0;
+    int precision = 0;
+    cudaStream_t user = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t g1 = nullptr, gN = nullptr;
+    char* ws = nullptr;
+    size_t bytes = 0;
+    Impl<float>* f = nullptr;
+    Impl<double>* d = nullptr;
+    double tol_host = 0.0;
+    std::vector<CaseStatus> st_host;
+};
+
+namespace {
+
+template <typename T>
+size_t plan(Impl<T>& im, int ncases, const hbugks_case* cases, char* base)
+{
+    Carver cv{base};
+    im.hc.resize(ncases);
+    im.dc.resize(ncases);
+    for (int k = 0; k < ncases; ++k) fill_host(im.hc[k], cases[k]);
+    im.d_cases = cv.take<CaseDev<T>>(ncases);
+    im.d_status = cv.take<CaseStatus>(ncases);
+    im.d_tol = cv.take<double>(1);
+    // N_T groups for the micro-update kernel (templated on N_T)
+    im.nt_groups.clear();
+    for (auto& h : im.hc)
+        if (std::find(im.nt_groups.begin(), im.nt_groups.end(), h.nt) == im.nt_groups.end())
+            im.nt_groups.push_back(h.nt);
+    im.n_off_tables = 4 + (int)im.nt_groups.size();
+    im.d_off = cv.take<int>((size_t)im.n_off_tables * (ncases + 1));
+    for (int k = 0; k < ncases; ++k) {
+        layout_case(cv, im.hc[k], im.dc[k]);
+        im.dc[k].st = im.d_status + k;
+        im.dc[k].tol = im.d_tol;
+    }
+    // block offset tables: 0 k1, 1 k2, 2 k3, 3 steps, 4.. k4 per N_T group
+    im.off_host.assign((size_t)im.n_off_tables * (ncases + 1), 0);
+    for (int t = 0; t < im.n_off_tables; ++t) {
+        int acc = 0;
+        for (int k = 0; k < ncases; ++k) {
+            im.off_host[(size_t)t * (ncases + 1) + k] = acc;
+            const HostCase& h = im.hc[k];
+            int nb = 0;
+            switch (t) {
+                case 0: nb = h.k1b; break;
+                case 1: nb = h.k2b; break;
+                case 2: nb = h.k3b; break;
+                case 3: nb = h.ksb; break;
+                default: nb = (h.nt == im.nt_groups[t - 4]) ? h.k4b : 0;
+            }
+            acc += nb;
+        }
+        im.off_host[(size_t)t * (ncases + 1) + ncases] = acc;
+        if (t < 4) im.tot[t] = acc;
+    }
+    im.k4tot.clear();
+    for (size_t g = 0; g < im.nt_groups.size(); ++g)
+        im.k4tot.push_back(im.off_host[(4 + g) * (ncases + 1) + ncases]);
+    return cv.off + 256;
+}
+
+// host tables of one case uploaded into the workspace
+template <typename T>
+cudaError_t upload_case(const HostCase& h, const CaseDev<T>& d, cudaStream_t s, std::vector<std::vector<char>>& keep)
+{
+    auto put = [&](const void* dst, const void* src, size_t n) -> cudaError_t {
+        keep.emplace_back((const char*)src, (const char*)src + n);
+        return cudaMemcpyAsync(const_cast<void*>(dst), keep.back().data(), n, cudaMemcpyHostToDevice, s);
+    };
+    cudaError_t e;
+    std::vector<double> xc(h.nx), yc(h.ny), hx(h.nx), hy(h.ny), rdx(h.nx, 0.0), rdy(h.ny, 0.0);
+    for (int i = 0; i < h.nx; ++i) { xc[i] = 0.5 * (h.xn[i] + h.xn[i + 1]); hx[i] = 0.5 * (h.xn[i + 1] - h.xn[i]); }
+    for (int j = 0; j < h.ny; ++j) { yc[j] = 0.5 * (h.yn[j] + h.yn[j + 1]); hy[j] = 0.5 * (h.yn[j + 1] - h.yn[j]); }
+    for (int i = 0; i + 1 < h.nx; ++i) rdx[i] = 1.0 / (xc[i + 1] - xc[i]);
+    for (int j = 0; j + 1 < h.ny; ++j) rdy[j] = 1.0 / (yc[j + 1] - yc[j]);
+    std::vector<double> vu(h.nvp, 0.0), vv(h.nvp, 0.0), vw(h.nvp, 0.0);
+    std::vector<T> tu(h.nvp, T(0)), tv(h.nvp, T(0)), tw(h.nvp, T(0)), th(h.nvp, T(0));
+    double ref[5][13];
+    memset(ref, 0, sizeof ref);
+    for (int jv = 0; jv < h.nv; ++jv)
+        for (int iu = 0; iu < h.nu; ++iu) {
+            int a = jv * h.nu + iu;
+            double u = h.u[iu], v = h.v[jv], w = h.wu[iu] * h.wv[jv];
+            vu[a] = u; vv[a] = v; vw[a] = w;
+            double href = (1.0 / M_PI) * exp(-(u * u + v * v));
+            double bref = 0.5 * href;
+            tu[a] = T(u); tv[a] = T(v); tw[a] = T(w); th[a] = T(href);
+            double m[13] = {href, u * href, v * href, u * u * href, u * v * href, v * v * href, u * u * u * href,
+                            u * u * v * href, u * v * v * href, v * v * v * href, bref, u * bref, v * bref};
+            bool in[5] = {true, u > 0, u < 0, v > 0, v < 0};
+            for (int s5 = 0; s5 < 5; ++s5)
+                if (in[s5])
+                    for (int k = 0; k < 13; ++k) ref[s5][k] += w * m[k];
+        }
+    if ((e = put(d.wall, h.wall_tab.data(), sizeof(double) * h.wall_tab.size()))) return e;
+    if ((e = put(d.xn, h.xn.data(), sizeof(double) * h.xn.size()))) return e;
+    if ((e = put(d.yn, h.yn.data(), sizeof(double) * h.yn.size()))) return e;
+    if ((e = put(d.xc, xc.data(), sizeof(double) * h.nx))) return e;
+    if ((e = put(d.yc, yc.data(), sizeof(double) * h.ny))) return e;
+    if ((e = put(d.hx, hx.data(), sizeof(double) * h.nx))) return e;
+    if ((e = put(d.hy, hy.data(), sizeof(double) * h.ny))) return e;
+    if ((e = put(d.rdx, rdx.data(), sizeof(double) * h.nx))) return e;
+    if ((e = put(d.rdy, rdy.data(), sizeof(double) * h.ny))) return e;
+    if ((e = put(d.vu, vu.data(), sizeof(double) * h.nvp))) return e;
+    if ((e = put(d.vv, vv.data(), sizeof(double) * h.nvp))) return e;
+    if ((e = put(d.vw, vw.data(), sizeof(double) * h.nvp))) return e;
+    if ((e = put(d.tu, tu.data(), sizeof(T) * h.nvp))) return e;
+    if ((e = put(d.tv, tv.data(), sizeof(T) * h.nvp))) return e;
+    if ((e = put(d.tw, tw.data(), sizeof(T) * h.nvp))) return e;
+    if ((e = put(d.thref, th.data(), sizeof(T) * h.nvp))) return e;
+    if ((e = put(d.u1, h.u.data(), sizeof(double) * h.nu))) return e;
+    if ((e = put(d.wu1, h.wu.data(), sizeof(double) * h.nu))) return e;
+    if ((e = put(d.v1, h.v.data(), sizeof(double) * h.nv))) return e;
+    if ((e = put(d.wv1, h.wv.data(), sizeof(double) * h.nv))) return e;
+    if ((e = put(d.refmom, &ref[0][0], sizeof ref))) return e;
+    return cudaSuccess;
+}
+
+__global__ void k_status_reset(CaseStatus* st, int ncases, int which, int user_active)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ncases || (which >= 0 && k != which)) return;
+    st[k].active = 0;
+    st[k].parity = 0;
+    st[k].diverged = 0;
+    st[k].iters = 0;
+    st[k].iters_call = 0;
+    if (user_active >= 0) st[k].user_active = user_active;
+    for (int q = 0; q < 4; ++q) st[k].last[q] = 0.0;
+}
+
+__global__ void k_begin_call(CaseStatus* st, int ncases)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ncases) return;
+    st[k].active = st[k].user_active && !st[k].diverged;
+    st[k].iters_call = 0;
+}
+
+template <typename T>
+void enqueue_iteration(Impl<T>& im, int ncases, cudaStream_t s)
+{
+    const int* off = im.d_off;
+    const int stride = ncases + 1;
+    if (im.tot[0]) k1_moments<T><<<im.tot[0], 256, 0, s>>>(Batch<T>{im.d_cases, ncases, off + 0 * stride});
+    if (im.tot[1]) k2_face_params<T><<<im.tot[1], 128, 0, s>>>(Batch<T>{im.d_cases, ncases, off + 1 * stride});
+    if (im.tot[2]) k3_macro<T><<<im.tot[2], K3_THREADS, 0, s>>>(Batch<T>{im.d_cases, ncases, off + 2 * stride});
+    for (size_t g = 0; g < im.nt_groups.size(); ++g) {
+        Batch<T> b{im.d_cases, ncases, off + (4 + g) * stride};
+        if (im.k4tot[g]) k4_micro<T><<<im.k4tot[g], 256, 0, s>>>(b);
+    }
+    k5_finish<T><<<ncases, 32, 0, s>>>(im.d_cases, ncases, off + 2 * stride);
+}
+
+template <typename T>
+void enqueue_steps(Impl<T>& im, int ncases, cudaStream_t s)
+{
+    if (im.tot[3]) k_steps<T><<<im.tot[3], 128, 0, s>>>(Batch<T>{im.d_cases, ncases, im.d_off + 3 * (ncases + 1)});
+}
+
+hbugks_status begin(hbugks_t h)
+{
+    HB_CK(cudaEventRecord(h->ev_in, h->user));
+    HB_CK(cudaStreamWaitEvent(h->s, h->ev_in, 0));
+    return HBUGKS_OK;
+}
+
+hbugks_status end(hbugks_t h)
+{
+    HB_CK(cudaEventRecord(h->ev_out, h->s));
+    HB_CK(cudaStreamWaitEvent(h->user, h->ev_out, 0));
+    HB_CK(cudaGetLastError());
+    return HBUGKS_OK;
+}
+
+template <typename T>
+hbugks_status capture(hbugks_t h, Impl<T>& im)
+{
+    for (int which = 0; which < 2; ++which) {
+        int n = which == 0 ? 1 : CHUNK;
+        cudaGraph_t g;
+        HB_CK(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < n; ++k) enqueue_iteration(im, h->ncases, h->s);
+        HB_CK(cudaStreamEndCapture(h->s, &g));
+        cudaGraphExec_t ex;
+        HB_CK(cudaGraphInstantiate(&ex, g, 0));
+        cudaGraphDestroy(g);
+        (which == 0 ? h->g1 : h->gN) = ex;
+    }
+    return HBUGKS_OK;
+}
+
+template <typename T>
+hbugks_status do_create(hbugks_t h, Impl<T>& im, int ncases, const hbugks_case* cases)
+{
+    plan(im, ncases, cases, h->ws);
+    std::vector<std::vector<char>> keep;
+    for (int k = 0; k < ncases; ++k) HB_CK(upload_case(im.hc[k], im.dc[k], h->s, keep));
+    HB_CK(cudaMemcpyAsync(im.d_cases, im.dc.data(), sizeof(CaseDev<T>) * ncases, cudaMemcpyHostToDevice, h->s));
+    HB_CK(cudaMemcpyAsync(im.d_off, im.off_host.data(), sizeof(int) * im.off_host.size(), cudaMemcpyHostToDevice, h->s));
+    HB_CK(cudaMemsetAsync(im.d_tol, 0, sizeof(double), h->s));
+    k_status_reset<<<(ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, ncases, -1, 1);
+    for (int k = 0; k < ncases; ++k) {
+        const CaseDev<T>& d = im.dc[k];
+        size_t tot = (size_t)d.nc * d.nvb * VB * d.nt;
+        k_init_uniform<T><<<(unsigned)((tot + 255) / 256), 256, 0, h->s>>>(d, 1.0, 0.0, 0.0, 1.0);
+    }
+    enqueue_steps(im, ncases, h->s);
+    HB_CK(cudaStreamSynchronize(h->s));
+    HB_CK(cudaGetLastError());
+    return capture(h, im);
+}
+
+template <class F>
+hbugks_status dispatch(hbugks_t h, F&& fn)
+{
+    if (h->f) return fn(*h->f);
+    return fn(*h->d);
+}
+
+}  // namespace
+
+// ====================================================================================== ABI
+
+extern "C" {
+
+size_t hbugks_workspace_bytes(int ncases, const hbugks_case* cases)
+{
+    if (ncases < 1 || !cases) return 0;
+    for (int k = 0; k < ncases; ++k)
+        if (!validate(cases[k]) || cases[k].phys.precision != cases[0].phys.precision) return 0;
+    if (cases[0].phys.precision == 1) {
+        Impl<float> im;
+        return plan(im, ncases, cases, nullptr);
+    }
+    Impl<double> im;
+    return plan(im, ncases, cases, nullptr);
+}
+
+hbugks_status hbugks_create(int ncases, const hbugks_case* cases, void* d_workspace, size_t bytes,
+                            void* cuda_stream, hbugks_t* out)
+{
+    if (!out || !d_workspace || ((uintptr_t)d_workspace & 255)) return HBUGKS_EINVAL;
+    size_t need = hbugks_workspace_bytes(ncases, cases);
+    if (need == 0) return HBUGKS_EINVAL;
+    if (bytes < need) return HBUGKS_ENOMEM;
+    hbugks_t h = new (std::nothrow) hbugks_solver;
+    if (!h) return HBUGKS_ENOMEM;
+    h->ncases = ncases;
+    h->precision = cases[0].phys.precision;
+    h->user = (cudaStream_t)cuda_stream;
+    h->ws = (char*)d_workspace;
+    h->bytes = bytes;
+    h->st_host.resize(ncases);
+    hbugks_status rc = HBUGKS_OK;
+    if (cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+        hbugks_destroy(h);
+        return HBUGKS_ECUDA;
+    }
+    if ((rc = begin(h)) != HBUGKS_OK) { hbugks_destroy(h); return rc; }
+    if (h->precision == 1) {
+        h->f = new Impl<float>;
+        rc = do_create(h, *h->f, ncases, cases);
+    } else {
+        h->d = new Impl<double>;
+        rc = do_create(h, *h->d, ncases, cases);
+    }
+    if (rc == HBUGKS_OK) rc = end(h);
+    if (rc != HBUGKS_OK) { hbugks_destroy(h); return rc; }
+    *out = h;
+    return HBUGKS_OK;
+}
+
+void hbugks_destroy(hbugks_t h)
+{
+    if (!h) return;
+    if (h->s) cudaStreamSynchronize(h->s);
+    if (h->g1) cudaGraphExecDestroy(h->g1);
+    if (h->gN) cudaGraphExecDestroy(h->gN);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->s) cudaStreamDestroy(h->s);
+    delete h->f;
+    delete h->d;
+    delete h;
+}
+
+hbugks_status hbugks_set_wall(hbugks_t h, int ci, int wall, const hbugks_wall* w)
+{
+    if (!h || !w || ci < 0 || ci >= h->ncases || wall < 0 || wall > 3) return HBUGKS_EINVAL;
+    return dispatch(h, [&](auto& im) -> hbugks_status {
+        HostCase hc = im.hc[ci];
+        hc.src.walls[wall] = *w;
+        if (!validate(hc.src)) return HBUGKS_EINVAL;
+        fill_host(im.hc[ci], hc.src);
+        hbugks_status rc = begin(h);
+        if (rc) return rc;
+        HB_CK(cudaMemcpyAsync((void*)im.dc[ci].wall, im.hc[ci].wall_tab.data(),
+                              sizeof(double) * im.hc[ci].wall_tab.size(), cudaMemcpyHostToDevice, h->s));
+        HB_CK(cudaStreamSynchronize(h->s));
+        return end(h);
+    });
+}
+
+hbugks_status hbugks_init_uniform(hbugks_t h, int ci, double rho, double u, double v, double T)
+{
+    if (!h || ci < -1 || ci >= h->ncases || !(rho > 0) || !(T > 0)) return HBUGKS_EINVAL;
+    return dispatch(h, [&](auto& im) -> hbugks_status {
+        hbugks_status rc = begin(h);
+        if (rc) return rc;
+        k_status_reset<<<(h->ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, h->ncases, ci, -1);
+        for (int k = 0; k < h->ncases; ++k) {
+            if (ci >= 0 && k != ci) continue;
+            auto& d = im.dc[k];
+            size_t tot = (size_t)d.nc * d.nvb * VB * d.nt;
+            using TT = typename std::remove_pointer<decltype(d.tu)>::type;
+            k_init_uniform<std::remove_const_t<TT>><<<(unsigned)((tot + 255) / 256), 256, 0, h->s>>>(d, rho, u, v, T);
+        }
+        enqueue_steps(im, h->ncases, h->s);
+        return end(h);
+    });
+}
+
+hbugks_status hbugks_set_state(hbugks_t h, int ci, const double* W, const double* hh, const double* bb)
+{
+    if (!h || ci < 0 || ci >= h->ncases || !W || !hh || !bb) return HBUGKS_EINVAL;
+    return dispatch(h, [&](auto& im) -> hbugks_status {
+        auto& d = im.dc[ci];
+        using TT = std::remove_const_t<typename std::remove_pointer<decltype(d.tu)>::type>;
+        hbugks_status rc = begin(h);
+        if (rc) return rc;
+        k_status_reset<<<(h->ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, h->ncases, ci, -1);
+        HB_CK(cudaMemcpyAsync(d.W[0], W, sizeof(double) * d.nt * d.nc * 4, cudaMemcpyHostToDevice, h->s));
+        const size_t lvl = (size_t)d.nc * d.nvel;
+        const size_t tot = (size_t)d.nc * d.nvb * VB;
+        for (int n = 0; n < d.nt; ++n)
+            for (int which = 0; which < 2; ++which) {
+                const double* src = (which == 0 ? hh : bb) + (size_t)n * lvl;
+                HB_CK(cudaMemcpyAsync(d.stage, src, sizeof(double) * lvl, cudaMemcpyHostToDevice, h->s));
+                k_set_level<TT><<<(unsigned)((tot + 255) / 256), 256, 0, h->s>>>(d, n, which, d.stage);
+            }
+        enqueue_steps(im, h->ncases, h->s);
+        HB_CK(cudaStreamSynchronize(h->s));
+        return end(h);
+    });
+}
+
+hbugks_status hbugks_get_state(hbugks_t h, int ci, double* W, double* hh, double* bb)
+{
+    if (!h || ci < 0 || ci >= h->ncases || !W || !hh || !bb) return HBUGKS_EINVAL;
+    return dispatch(h, [&](auto& im) -> hbugks_status {
+        auto& d = im.dc[ci];
+        using TT = std::remove_const_t<typename std::remove_pointer<decltype(d.tu)>::type>;
+        hbugks_status rc = begin(h);
+        if (rc) return rc;
+        CaseStatus st;
+        HB_CK(cudaMemcpyAsync(&st, im.d_status + ci, sizeof st, cudaMemcpyDeviceToHost, h->s));
+        HB_CK(cudaStreamSynchronize(h->s));
+        HB_CK(cudaMemcpyAsync(W, d.W[st.parity], sizeof(double) * d.nt * d.nc * 4, cudaMemcpyDeviceToHost, h->s));
+        const size_t lvl = (size_t)d.nc * d.nvel;
+        const size_t tot = (size_t)d.nc * d.nvb * VB;
+        for (int n = 0; n < d.nt; ++n)
+            for (int which = 0; which < 2; ++which) {
+                k_get_level<TT><<<(unsigned)((tot + 255) / 256), 256, 0, h->s>>>(d, n, which, d.stage);
+                double* dst = (which == 0 ? hh : bb) + (size_t)n * lvl;
+                HB_CK(cudaMemcpyAsync(dst, d.stage, sizeof(double) * lvl, cudaMemcpyDeviceToHost, h->s));
+            }
+        HB_CK(cudaStreamSynchronize(h->s));
+        return end(h);
+    });
+}
+
+hbugks_status hbugks_set_active(hbugks_t h, const int* flags)
+{
+    if (!h || !flags) return HBUGKS_EINVAL;
+    return dispatch(h, [&](auto& im) -> hbugks_status {
+        hbugks_status rc = begin(h);
+        if (rc) return rc;
+        std::vector<CaseStatus> st(h->ncases);
+        HB_CK(cudaMemcpyAsync(st.data(), im.d_status, sizeof(CaseStatus) * h->ncases, cudaMemcpyDeviceToHost, h->s));
+        HB_CK(cudaStreamSynchronize(h->s));
+        for (int k = 0; k < h->ncases; ++k) st[k].user_active = flags[k] ? 1 : 0;
+        HB_CK(cudaMemcpyAsync(im.d_status, st.data(), sizeof(CaseStatus) * h->ncases, cudaMemcpyHostToDevice, h->s));
+        HB_CK(cudaStreamSynchronize(h->s));
+        return end(h);
+    });
+}
+
+static hbugks_status launch_iters(hbugks_t h, int n)
+{
+    while (n >= CHUNK) {
+        HB_CK(cudaGraphLaunch(h->gN, h->s));
+        n -= CHUNK;
+    }
+    while (n-- > 0) HB_CK(cudaGraphLaunch(h->g1, h->s));
+    return HBUGKS_OK;
+}
+
+hbugks_status hbugks_enqueue_iterations(hbugks_t h, int n)
+{
+    if (!h || n < 0) return HBUGKS_EINVAL;
+    return dispatch(h, [&](auto& im) -> hbugks_status {
+        hbugks_status rc = begin(h);
+        if (rc) return rc;
+        HB_CK(cudaMemsetAsync(im.d_tol, 0, sizeof(double), h->s));
+        k_begin_call<<<(h->ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, h->ncases);
+        if ((rc = launch_iters(h, n))) return rc;
+        return end(h);
+    });
+}
+
+hbugks_status hbugks_iterate(hbugks_t h, int max_iters, double tol_rho, int* iters_done, double* resid_out)
+{
+    if (!h || max_iters < 0) return HBUGKS_EINVAL;
+    return dispatch(h, [&](auto& im) -> hbugks_status {
+        hbugks_status rc = begin(h);
+        if (rc) return rc;
+        h->tol_host = tol_rho > 0 ? tol_rho : 0.0;
+        HB_CK(cudaMemcpyAsync(im.d_tol, &h->tol_host, sizeof(double), cudaMemcpyHostToDevice, h->s));
+        k_begin_call<<<(h->ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, h->ncases);
+        int done = 0;
+        std::vector<CaseStatus>& st = h->st_host;
+        while (done < max_iters) {
+            int n = std::min(CHUNK, max_iters - done);
+            if ((rc = launch_iters(h, n))) return rc;
+            done += n;
+            HB_CK(cudaMemcpyAsync(st.data(), im.d_status, sizeof(CaseStatus) * h->ncases, cudaMemcpyDeviceToHost, h->s));
+            HB_CK(cudaStreamSynchronize(h->s));
+            bool any = false;
+            for (int k = 0; k < h->ncases; ++k) any = any || st[k].active;
+            if (!any) break;
+        }
+        if (done == 0) {
+            HB_CK(cudaMemcpyAsync(st.data(), im.d_status, sizeof(CaseStatus) * h->ncases, cudaMemcpyDeviceToHost, h->s));
+            HB_CK(cudaStreamSynchronize(h->s));
+        }
+        bool diverged = false, all = true;
+        for (int k = 0; k < h->ncases; ++k) {
+            if (iters_done) iters_done[k] = (int)st[k].iters_call;
+            if (resid_out)
+                for (int q = 0; q < 4; ++q) resid_out[k * 4 + q] = st[k].last[q];
+            if (st[k].diverged) diverged = true;
+            if (tol_rho > 0 && st[k].user_active && !(st[k].last[0] <= tol_rho && st[k].iters >= 10)) all = false;
+        }
+        if ((rc = end(h))) return rc;
+        if (diverged) return HBUGKS_DIVERGED;
+        return all ? HBUGKS_OK : HBUGKS_NOT_CONVERGED;
+    });
+}
+
+hbugks_status hbugks_residual_history(hbugks_t h, int ci, int n, double* out)
+{
+    if (!h || ci < 0 || ci >= h->ncases || n < 0 || n > RING || !out) return HBUGKS_EINVAL;
+    return dispatch(h, [&](auto& im) -> hbugks_status {
+        hbugks_status rc = begin(h);
+        if (rc) return rc;
+        std::vector<double> ring((size_t)RING * 4);
+        CaseStatus st;
+        HB_CK(cudaMemcpyAsync(ring.data(), im.dc[ci].rhist, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost, h->s));
+        HB_CK(cudaMemcpyAsync(&st, im.d_status + ci, sizeof st, cudaMemcpyDeviceToHost, h->s));
+        HB_CK(cudaStreamSynchronize(h->s));
+        if (n > st.iters) return HBUGKS_EINVAL;
+        for (int k = 0; k < n; ++k) {
+            long long it = st.iters - n + k;
+            for (int q = 0; q < 4; ++q) out[k * 4 + q] = ring[(it % RING) * 4 + q];
+        }
+        return end(h);
+    });
+}
+
+hbugks_status hbugks_get_level_fields(hbugks_t h, int ci, int level, double* out)
+{
+    if (!h || ci < 0 || ci >= h->ncases || !out) return HBUGKS_EINVAL;
+    return dispatch(h, [&](auto& im) -> hbugks_status {
+        auto& d = im.dc[ci];
+        using TT = std::remove_const_t<typename std::remove_pointer<decltype(d.tu)>::type>;
+        if (level < 0 || level >= d.nt) return HBUGKS_EINVAL;
+        hbugks_status rc = begin(h);
+        if (rc) return rc;
+        k_fields<TT><<<(d.nc + 7) / 8, 256, 0, h->s>>>(d, level, d.stage);
+        HB_CK(cudaMemcpyAsync(out, d.stage, sizeof(double) * 8 * d.nc, cudaMemcpyDeviceToHost, h->s));
+        HB_CK(cudaStreamSynchronize(h->s));
+        return end(h);
+    });
+}
+
+hbugks_status hbugks_get_harmonic(hbugks_t h, int ci, int k, double* re, double* im_out)
+{
+    if (!h || ci < 0 || ci >= h->ncases || !re || !im_out) return HBUGKS_EINVAL;
+    return dispatch(h, [&](auto& im) -> hbugks_status {
+        auto& d = im.dc[ci];
+        using TT = std::remove_const_t<typename std::remove_pointer<decltype(d.tu)>::type>;
+        if (k < 0 || k > d.nh) return HBUGKS_EINVAL;
+        hbugks_status rc = begin(h);
+        if (rc) return rc;
+        for (int n = 0; n < d.nt; ++n)
+            k_fields<TT><<<(d.nc + 7) / 8, 256, 0, h->s>>>(d, n, d.stage + (size_t)n * 8 * d.nc);
+        double* ore = d.stage + (size_t)d.nt * 8 * d.nc;
+        double* oim = ore + 8 * d.nc;
+        k_dft<<<(8 * d.nc + 127) / 128, 128, 0, h->s>>>(d.stage, d.nt, d.nc, k, ore, oim);
+        HB_CK(cudaMemcpyAsync(re, ore, sizeof(double) * 8 * d.nc, cudaMemcpyDeviceToHost, h->s));
+        HB_CK(cudaMemcpyAsync(im_out, oim, sizeof(double) * 8 * d.nc, cudaMemcpyDeviceToHost, h->s));
+        HB_CK(cudaStreamSynchronize(h->s));
+        return end(h);
+    });
+}
+
+long long hbugks_iteration_count(hbugks_t h, int ci)
+{
+    if (!h || ci < 0 || ci >= h->ncases) return -1;
+    CaseStatus st;
+    const CaseStatus* src = h->f ? h->f->d_status + ci : h->d->d_status + ci;
+    if (begin(h) != HBUGKS_OK) return -1;
+    if (cudaMemcpyAsync(&st, src, sizeof st, cudaMemcpyDeviceToHost, h->s) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(h->s) != cudaSuccess) return -1;
+    if (end(h) != HBUGKS_OK) return -1;
+    return st.iters;
+}
+
+int hbugks_launches_per_iteration(hbugks_t h)
+{
+    if (!h) return -1;
+    int g = h->f ? (int)h->f->nt_groups.size() : (int)h->d->nt_groups.size();
+    return 4 + g;
+}
+
+const char* hbugks_status_string(hbugks_status s)
+{
+    switch (s) {
+        case HBUGKS_OK: return "ok";
+        case HBUGKS_NOT_CONVERGED: return "not converged";
+        case HBUGKS_EINVAL: return "invalid argument";
+        case HBUGKS_ECUDA: return "CUDA error";
+        case HBUGKS_ENOMEM: return "workspace too small";
+        case HBUGKS_DIVERGED: return "diverged";
+        case HBUGKS_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,62 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every symbol include/hbugks.h declares, and
+its host-side validation rejects invalid cases (no GPU compute is called)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2605_03479_gb300 import build, hbugks, inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return hbugks.lib()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "hbugks.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hbugks_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_names():
+    assert declared_symbols() == sorted(hbugks.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+        assert isinstance(getattr(L, name), ctypes._CFuncPtr)
+
+
+def test_status_strings(L):
+    assert hbugks.status_string(0) == "ok"
+    assert hbugks.status_string(-4) == "diverged"
+    assert hbugks.status_string(123) == "unknown status"
+
+
+def test_workspace_size_and_validation(L):
+    c = I.config1()
+    n = hbugks.workspace_bytes([c])
+    # state: 2 buffers x (h, b) x nt * nc * nvel doubles, plus W and tables
+    assert n > 4 * c.nt * c.nc * c.nvel * 8
+    c32 = I.config1()
+    c32.precision = 1
+    assert hbugks.workspace_bytes([c32]) < n
+    bad = I.config1()
+    bad.xnodes = bad.xnodes[::-1].copy()              # decreasing nodes
+    assert hbugks.workspace_bytes([bad]) == 0
+    bad = I.config1()
+    bad.n_harmonics = 8                                # N_T = 17 > 15
+    assert hbugks.workspace_bytes([bad]) == 0
+    bad = I.config1()
+    bad.walls[2][2] = -1.0                             # negative wall temperature
+    assert hbugks.workspace_bytes([bad]) == 0
+    mixed = [I.config1(), c32]                         # one handle, one precision
+    assert hbugks.workspace_bytes(mixed) == 0
+    assert hbugks.workspace_bytes(I.config4_cases()) > 0
