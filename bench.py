@@ -1,0 +1,268 @@
+#!/usr/bin/env python
+"""Benchmark of the HB-UGKS pseudo-time iteration on GB300 (one JSON line on rank 0).
+
+A step is one pseudo-time iteration of HB-UGKS over every cell, discrete velocity and sub-time level of
+the workload (face moments, interface parameters, macro update, micro update, residual).  The default
+workload is the large thermally driven cavity: 128x128 cells, 64x64 velocities, Shakhov Pr 2/3, bottom wall
+T0 (1 + 0.5 sin wt), Kn 0.05, St 5, N_H 5 (N_T 11), FP32-split storage (5.9 GB of distribution state, far
+larger than L2, so no flush is needed between timed steps).  The metric is cell.velocity.level updates/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+--impl reference times the FP64 CPU oracle (the method written plainly from the paper, single thread) on
+a bounded sample of the same workload: the same velocity grid, N_T and parameters on an 8x8-cell cavity.
+With torchrun (N > 1) every rank runs its own replica of the workload (the path has no data exchange
+between cases); value counts the updates of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HB-UGKS cell*velocity*level updates/s"
+UNIT = "updates/s"
+
+
+def workloads():
+    from paper_2605_03479_gb300 import inputs as I
+    return {
+        "thermal128_v64_nh5_fp32split": lambda: I.config5(precision=1),
+        "thermal128_v64_nh5_fp64": lambda: I.config5(precision=0),
+        "thermal64_v48_nh3_fp32split": lambda: I.config3(precision=1),
+        "shear32_v24_nh1_fp64": I.config1,
+    }
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(self.idx), "-lms", "100"], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.15)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            return None
+        sms, maxs, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sms.append(float(f[1]))
+                maxs.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def oracle_sample(case_full):
+    """The oracle's bounded sample of the workload: same velocity grid, N_T and physics on 8x8 cells."""
+    from paper_2605_03479_gb300 import inputs as I
+    c = I.make_case("sample8x8", 8, case_full.nu, kn=case_full.kn, st=case_full.st, nh=case_full.n_harmonics,
+                    pr=case_full.pr, drive="rest", half_width=case_full.umax)
+    c.walls = [list(w) for w in case_full.walls]
+    return c
+
+
+def run_oracle(case_full, steps, warmup, min_seconds=0.0):
+    from oracle import oracle as O
+    from paper_2605_03479_gb300 import inputs as I
+    c = oracle_sample(case_full)
+    P = O.Problem(c)
+    W, h, b = I.initial_state(c)
+    for _ in range(warmup):
+        O.iterate(P, W, h, b, 1)
+    t0 = time.perf_counter()
+    n = 0
+    while n < steps or (time.perf_counter() - t0) < min_seconds:
+        O.iterate(P, W, h, b, 1)
+        n += 1
+    dt = time.perf_counter() - t0
+    ups = c.updates_per_iteration() * n / dt
+    sample = (f"{c.nx}x{c.ny}-cell cavity with the workload's {c.nu}x{c.nv} velocity grid, N_T {c.nt}, "
+              f"Kn {c.kn:g}, St {c.st:g}, Pr {c.pr:.3g}, same walls; {n} iterations, "
+              f"{c.updates_per_iteration()} updates each")
+    return ups, dt / n, sample
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default="thermal128_v64_nh5_fp32split")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    case = workloads()[args.workload]()
+    W_ = max(args.warmup, 3)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        ups, sec, sample = run_oracle(case, args.steps, W_)
+        line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                "warmup": W_, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+                "config": {"workload": args.workload + " (oracle sample)", "sample": sample},
+                "cpu_baseline": {"value": ups, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                "e2e": {"value": ups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    from paper_2605_03479_gb300 import hbugks as hb
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = f"cuda:{local}"
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    s = hb.Solver(case, device=dev, stream=stream)
+    s.init_uniform(-1, 1.0, 0.0, 0.0, 1.0)
+    s.enqueue_iterations(W_)
+    torch.cuda.synchronize()
+
+    clk = Clocks(torch.cuda.current_device())
+    clk.start()
+    time.sleep(0.25)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.enqueue_iterations(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    upd = case.updates_per_iteration()
+    value = upd * world / (ms * 1e-3)
+    launches = s.launches_per_iteration() * args.steps + 1
+
+    # per-kernel times (CUDA events around each launch on the kernels' stream), roofline of the top kernel
+    kms = s.profile_kernels(3)
+    names = ("face_moments", "face_params", "macro_update", "micro_update", "residual")
+    top = int(np.argmax(kms))
+    bytes_per_update = 16 if case.precision == 1 else 32      # read + write of (h, b), each once
+    peak, peak_kind = peaks()
+    alg = {"micro_update": bytes_per_update, "face_moments": bytes_per_update // 2}
+    roof = None
+    if names[top] in alg:
+        ach = alg[names[top]] * upd / (kms[top] * 1e-3) / 1e9
+        roof = {"kernel": names[top], "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_source": peak_kind, "traffic": None,
+                "algorithmic_bytes_per_update": alg[names[top]]}
+    kernel_ms = {n: float(v) for n, v in zip(names, kms)}
+
+    # end to end through the public API: upload the initial state from pinned host memory, iterate, read back
+    # every harmonic field
+    e2e = None
+    if not args.no_e2e:
+        nt, nc, nv = case.nt, case.nc, case.nvel
+        from paper_2605_03479_gb300 import inputs as I
+        Wr, hr, br = I.initial_state(I.make_case("one", 1, case.nu, kn=case.kn, st=case.st,
+                                                 nh=case.n_harmonics, drive="rest", half_width=case.umax))
+        Wp = torch.empty((nt, nc, 4), dtype=torch.float64, pin_memory=True)
+        hp = torch.empty((nt, nc, nv), dtype=torch.float64, pin_memory=True)
+        bp = torch.empty((nt, nc, nv), dtype=torch.float64, pin_memory=True)
+        Wp.copy_(torch.from_numpy(Wr[:, :1, :]).expand(nt, nc, 4))
+        hp.copy_(torch.from_numpy(hr[:, :1, :]).expand(nt, nc, nv))
+        bp.copy_(torch.from_numpy(br[:, :1, :]).expand(nt, nc, nv))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.set_state(0, Wp.numpy(), hp.numpy(), bp.numpy())
+        rc, its, res = s.iterate(args.steps)
+        outs = [s.harmonic(0, k) for k in range(case.n_harmonics + 1)]
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        h2d = Wp.numel() * 8 + hp.numel() * 8 + bp.numel() * 8
+        d2h = sum(o.size * 16 for o in outs) + 32 * math.ceil(args.steps / 16)
+        e2e = {"value": upd * world * args.steps / dt, "unit": UNIT,
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "what": ("set_state from pinned host FP64 arrays + iterate(steps) with residual reads + all "
+                        "harmonic fields to host, host wall clock")}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        ups, sec, sample = run_oracle(case, 2, 0, min_seconds=10.0)
+        cpu = {"value": ups, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": W_, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32-split" if case.precision == 1 else "f64",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "cells": [case.nx, case.ny], "velocities": [case.nu, case.nv],
+                           "n_levels": case.nt, "kn": case.kn, "st": case.st, "pr": case.pr,
+                           "updates_per_step": upd, "parallelism": f"replicas{world}" if world > 1 else "single",
+                           "l2": "state larger than L2 (no flush needed)"},
+                "roofline": roof, "kernel_ms": kernel_ms, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    s.destroy()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -162,6 +162,11 @@ HBUGKS_API const char* hbugks_status_string(hbugks_status s);
  * synchronisation or residual check (for timing with CUDA events around the call). */
 HBUGKS_API hbugks_status hbugks_enqueue_iterations(hbugks_t h, int n);
 
+/* Kernel timing: run `n` iterations kernel by kernel (not graph-captured) with a CUDA event pair around each
+ * launch on the stream the kernels run on, synchronise, and write the average milliseconds per iteration of
+ * each kernel kind into ms[5]: face moments, face parameters, macro update, micro update, residual. */
+HBUGKS_API hbugks_status hbugks_profile_kernels(hbugks_t h, int n, double* ms);
+
 /* Number of kernel launches one iteration enqueues for this handle. */
 HBUGKS_API int hbugks_launches_per_iteration(hbugks_t h);
 

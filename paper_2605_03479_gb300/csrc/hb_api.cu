@@ -12,6 +12,7 @@
 
 #include "hbugks.h"
 #include "hb_kernels.cuh"
+#include "hb_tiles.cuh"
 
 using namespace hb;
 
@@ -54,8 +55,51 @@ struct HostCase {
     std::vector<double> xn, yn, u, wu, v, wv;
     double mu0, omega;
     std::vector<double> wall_tab;   // [4][nt][3]
-    int k1b, k2b, k3b, k4b, ksb;
+    int k1b, k2b, k3b, k4b, ksb, ktb;
+    int k1shape, k4shape;
 };
+
+// tile shapes of the tiled kernels: K4 (TX, TY), K1 (TX, TY, velocity blocks staged per pass)
+struct Shape {
+    int tx, ty, g;
+};
+constexpr Shape K4_SHAPES[] = {{4, 4, 0}, {4, 2, 0}, {2, 2, 0}};
+constexpr int N_K4_SHAPES = 3;
+constexpr Shape K1_SHAPES[] = {{4, 4, 6}, {4, 4, 3}};
+constexpr int N_K1_SHAPES = 2;
+
+template <typename T>
+size_t k4_smem_of(int shape, int nt)
+{
+    switch (shape) {
+        case 0: return k4_smem<T, 4, 4>(nt);
+        case 1: return k4_smem<T, 4, 2>(nt);
+        default: return k4_smem<T, 2, 2>(nt);
+    }
+}
+
+template <typename T>
+size_t k1_smem_of(int shape)
+{
+    return shape == 0 ? k1_smem<T, 4, 4, 6>() : k1_smem<T, 4, 4, 3>();
+}
+
+// largest tile whose shared memory lets two CTAs share an SM, else the largest that fits at all
+template <typename T>
+int pick_k4_shape(int nt)
+{
+    for (int s = 0; s < N_K4_SHAPES; ++s)
+        if (k4_smem_of<T>(s, nt) <= 113 * 1024) return s;
+    for (int s = 0; s < N_K4_SHAPES; ++s)
+        if (k4_smem_of<T>(s, nt) <= 227 * 1024) return s;
+    return -1;
+}
+
+template <typename T>
+int pick_k1_shape()
+{
+    return k1_smem_of<T>(0) <= 113 * 1024 ? 0 : 1;
+}
 
 bool validate(const hbugks_case& c)
 {
@@ -116,11 +160,10 @@ void fill_host(HostCase& h, const hbugks_case& c)
             o[1] = W.v_mean + W.v_re * cs - W.v_im * sn;
             o[2] = W.T_mean + W.T_re * cs - W.T_im * sn;   // Eq. bc_temp
         }
-    h.k1b = ((h.nf + h.nc) * h.nt + 7) / 8;
     h.k2b = (h.nf * h.nt + 127) / 128;
     h.k3b = (h.nc + K3_THREADS - 1) / K3_THREADS;
-    h.k4b = (h.nc * h.nvb + 7) / 8;
     h.ksb = (h.nc + 127) / 128;
+    h.ktb = (h.nc * h.nt + 3) / 4;
 }
 
 template <typename T>
@@ -134,6 +177,7 @@ void layout_case(Carver& cv, const HostCase& h, CaseDev<T>& d)
     d.lam0 = 1.0;
     for (int k = 0; k < 8; ++k) d.e[k] = 0.0;
     for (int dd = 1; dd <= h.nh; ++dd) d.e[dd] = ((dd & 1) ? -0.5 : 0.5) / sin(M_PI * dd / h.nt);   // Eq. D_explicit
+    for (int k = 0; k < 8; ++k) d.et[k] = T(d.e[k]);
     d.wall = cv.take<double>(4 * h.nt * 3);
     d.xn = cv.take<double>(h.nx + 1); d.yn = cv.take<double>(h.ny + 1);
     d.xc = cv.take<double>(h.nx); d.yc = cv.take<double>(h.ny);
@@ -143,6 +187,7 @@ void layout_case(Carver& cv, const HostCase& h, CaseDev<T>& d)
     d.tu = cv.take<T>(h.nvp); d.tv = cv.take<T>(h.nvp); d.tw = cv.take<T>(h.nvp); d.thref = cv.take<T>(h.nvp);
     d.u1 = cv.take<double>(h.nu); d.wu1 = cv.take<double>(h.nu);
     d.v1 = cv.take<double>(h.nv); d.wv1 = cv.take<double>(h.nv);
+    d.tu1 = cv.take<T>(h.nu); d.tv1 = cv.take<T>(h.nv);
     d.refmom = cv.take<double>(5 * 13);
     const size_t ns = (size_t)h.nvb * h.nc * h.nt * VB;
     for (int k = 0; k < 2; ++k) {
@@ -154,6 +199,20 @@ void layout_case(Carver& cv, const HostCase& h, CaseDev<T>& d)
     d.fmom = cv.take<double>((size_t)h.nf * h.nt * NM);
     d.cmom = cv.take<double>((size_t)h.nc * h.nt * NCM);
     d.fpar = cv.take<T>((size_t)h.nf * h.nt * NP);
+    d.ftab = cv.take<T>((size_t)h.nf * h.nt * (h.nu + h.nv));
+    d.wtab = cv.take<T>((size_t)4 * h.nt * (h.nu + h.nv));
+    d.wxr = cv.take<T>((size_t)9 * h.nu);
+    d.wyr = cv.take<T>((size_t)9 * h.nv);
+    d.xr0 = cv.take<double>(36);
+    d.yr0 = cv.take<double>(36);
+    d.xr0t = cv.take<T>(36);
+    d.yr0t = cv.take<T>(36);
+    d.wconst = cv.take<double>((size_t)4 * h.nt * WCN);
+    d.oconst = cv.take<double>(32);
+    d.ctab = cv.take<T>((size_t)h.nc * h.nt * 2 * (h.nu + h.nv));
+    d.viu = cv.take<int>(h.nvp);
+    d.viv = cv.take<int>(h.nvp);
+    d.shakhov = h.src.phys.pr != 1.0;
     d.fflux = cv.take<double>((size_t)h.nf * h.nt * 4);
     d.cpar = cv.take<T>((size_t)h.nc * h.nt * NCP);
     d.rpart = cv.take<double>((size_t)h.k3b * 4);
@@ -166,8 +225,13 @@ void layout_case(Carver& cv, const HostCase& h, CaseDev<T>& d)
 
 // ====================================================================================== solver
 
-struct SolverBase {
-    virtual ~SolverBase() {}
+// one kernel launch of the iteration covering every case it applies to
+struct LaunchSpec {
+    int kind;      // 0 K1 tile, 1 K2, 2 K3, 3 tables, 4 K4 tile, 5 steps
+    int shape;     // tile shape index (K1, K4)
+    int table;     // block offset table index
+    int total;     // total blocks
+    size_t smem;   // dynamic shared memory bytes
 };
 
 template <typename T>
@@ -177,12 +241,11 @@ struct Impl {
     CaseDev<T>* d_cases = nullptr;
     CaseStatus* d_status = nullptr;
     double* d_tol = nullptr;
-    int* d_off = nullptr;            // [kernel][ncases + 1]
+    int* d_err = nullptr;
+    int* d_off = nullptr;            // [table][ncases + 1]
     std::vector<int> off_host;
-    std::vector<int> nt_groups;      // distinct N_T values
-    int n_off_tables = 0;
-    int tot[5] = {0, 0, 0, 0, 0};    // total blocks of k1, k2, k3, ksteps per batch
-    std::vector<int> k4tot;          // per N_T group
+    std::vector<LaunchSpec> specs;   // in launch order (without the residual kernel)
+    int k3_table = 0, steps_table = 0;
 };
 
 struct hbugks_solver {
@@ -208,46 +271,118 @@ size_t plan(Impl<T>& im, int ncases, const hbugks_case* cases, char* base)
     Carver cv{base};
     im.hc.resize(ncases);
     im.dc.resize(ncases);
-    for (int k = 0; k < ncases; ++k) fill_host(im.hc[k], cases[k]);
+    for (int k = 0; k < ncases; ++k) {
+        HostCase& h = im.hc[k];
+        fill_host(h, cases[k]);
+        h.k1shape = pick_k1_shape<T>();
+        h.k4shape = pick_k4_shape<T>(h.nt);
+        const Shape s1 = K1_SHAPES[h.k1shape], s4 = K4_SHAPES[h.k4shape < 0 ? 0 : h.k4shape];
+        h.k1b = ((h.nx + s1.tx - 1) / s1.tx) * ((h.ny + s1.ty - 1) / s1.ty) * h.nt;
+        h.k4b = ((h.nx + s4.tx - 1) / s4.tx) * ((h.ny + s4.ty - 1) / s4.ty) * h.nvb;
+    }
     im.d_cases = cv.take<CaseDev<T>>(ncases);
     im.d_status = cv.take<CaseStatus>(ncases);
     im.d_tol = cv.take<double>(1);
-    // N_T groups for the micro-update kernel (templated on N_T)
-    im.nt_groups.clear();
-    for (auto& h : im.hc)
-        if (std::find(im.nt_groups.begin(), im.nt_groups.end(), h.nt) == im.nt_groups.end())
-            im.nt_groups.push_back(h.nt);
-    im.n_off_tables = 4 + (int)im.nt_groups.size();
-    im.d_off = cv.take<int>((size_t)im.n_off_tables * (ncases + 1));
+    im.d_err = cv.take<int>(1);
+    // launch specs: K1 per shape, K2, K3, tables, K4 per shape; plus the step kernel (state setting only)
+    im.specs.clear();
+    auto add = [&](int kind, int shape) { im.specs.push_back(LaunchSpec{kind, shape, (int)im.specs.size(), 0, 0}); };
+    for (int sh = 0; sh < N_K1_SHAPES; ++sh)
+        for (auto& h : im.hc)
+            if (h.k1shape == sh) { add(0, sh); break; }
+    add(1, 0);
+    add(2, 0);
+    im.k3_table = (int)im.specs.size() - 1;
+    add(3, 0);
+    for (int sh = 0; sh < N_K4_SHAPES; ++sh)
+        for (auto& h : im.hc)
+            if (h.k4shape == sh) { add(4, sh); break; }
+    add(5, 0);
+    im.steps_table = (int)im.specs.size() - 1;
+    const int ntab = (int)im.specs.size();
+    im.d_off = cv.take<int>((size_t)ntab * (ncases + 1));
     for (int k = 0; k < ncases; ++k) {
         layout_case(cv, im.hc[k], im.dc[k]);
         im.dc[k].st = im.d_status + k;
         im.dc[k].tol = im.d_tol;
+        im.dc[k].err = im.d_err;
     }
-    // block offset tables: 0 k1, 1 k2, 2 k3, 3 steps, 4.. k4 per N_T group
-    im.off_host.assign((size_t)im.n_off_tables * (ncases + 1), 0);
-    for (int t = 0; t < im.n_off_tables; ++t) {
+    im.off_host.assign((size_t)ntab * (ncases + 1), 0);
+    for (auto& sp : im.specs) {
         int acc = 0;
+        size_t smem = 0;
         for (int k = 0; k < ncases; ++k) {
-            im.off_host[(size_t)t * (ncases + 1) + k] = acc;
+            im.off_host[(size_t)sp.table * (ncases + 1) + k] = acc;
             const HostCase& h = im.hc[k];
             int nb = 0;
-            switch (t) {
-                case 0: nb = h.k1b; break;
+            switch (sp.kind) {
+                case 0: if (h.k1shape == sp.shape) { nb = h.k1b; smem = std::max(smem, k1_smem_of<T>(sp.shape)); } break;
                 case 1: nb = h.k2b; break;
                 case 2: nb = h.k3b; break;
-                case 3: nb = h.ksb; break;
-                default: nb = (h.nt == im.nt_groups[t - 4]) ? h.k4b : 0;
+                case 3: nb = h.ktb; break;
+                case 4: if (h.k4shape == sp.shape) { nb = h.k4b; smem = std::max(smem, k4_smem_of<T>(sp.shape, h.nt)); } break;
+                case 5: nb = h.ksb; break;
             }
             acc += nb;
         }
-        im.off_host[(size_t)t * (ncases + 1) + ncases] = acc;
-        if (t < 4) im.tot[t] = acc;
+        im.off_host[(size_t)sp.table * (ncases + 1) + ncases] = acc;
+        sp.total = acc;
+        sp.smem = smem;
     }
-    im.k4tot.clear();
-    for (size_t g = 0; g < im.nt_groups.size(); ++g)
-        im.k4tot.push_back(im.off_host[(4 + g) * (ncases + 1) + ncases]);
     return cv.off + 256;
+}
+
+// Constants of the diffuse walls, FP64 on the host (they depend only on the wall waveforms):
+//   wconst[w][n]: raw moments of the unit-density wall Maxwellian H_w (and B_w = H_w / (2 lam_w)) over the
+//                 reflected velocities (13), sum_refl w |u_n| H_w, and the reflected flux moments of (H_w, B_w) (4);
+//   oconst[w]:    incident and reflected flux moments of (H_ref, B_ref);
+//   wtab[w][n]:   expm1(lam0 x^2 - lam_w (x - U_w)^2) over the 1-D nodes (separable wall Maxwellian).
+template <typename T>
+void wall_constants(const HostCase& h, std::vector<double>& wconst, std::vector<double>& oconst, std::vector<T>& wtab)
+{
+    const int nt = h.nt, nuv = h.nu + h.nv;
+    wconst.assign((size_t)4 * nt * WCN, 0.0);
+    oconst.assign(32, 0.0);
+    wtab.assign((size_t)4 * nt * nuv, T(0));
+    for (int wl = 0; wl < 4; ++wl) {
+        const int ax = (wl == 1 || wl == 3) ? 0 : 1;        // right/left walls are x-normal
+        const double nin = (wl == 0 || wl == 3) ? 1.0 : -1.0;
+        for (int n = 0; n < nt; ++n) {
+            const double* ws = &h.wall_tab[(wl * nt + n) * 3];
+            const double Uw = ws[0], Vw = ws[1], lamw = 1.0 / ws[2];
+            double* o = &wconst[((size_t)wl * nt + n) * WCN];
+            for (int jv = 0; jv < h.nv; ++jv)
+                for (int iu = 0; iu < h.nu; ++iu) {
+                    const double u = h.u[iu], v = h.v[jv], w = h.wu[iu] * h.wv[jv];
+                    const double un = ax == 0 ? u : v;
+                    if (!(un * nin > 0)) continue;
+                    const double H = lamw / M_PI * exp(-lamw * ((u - Uw) * (u - Uw) + (v - Vw) * (v - Vw)));
+                    const double B = H * 0.5 / lamw;
+                    const double m[13] = {H, u * H, v * H, u * u * H, u * v * H, v * v * H, u * u * u * H,
+                                          u * u * v * H, u * v * v * H, v * v * v * H, B, u * B, v * B};
+                    for (int k = 0; k < 13; ++k) o[k] += w * m[k];
+                    o[13] += w * fabs(un) * H;
+                    o[14] += w * un * H;
+                    o[15] += w * un * u * H;
+                    o[16] += w * un * v * H;
+                    o[17] += w * un * 0.5 * ((u * u + v * v) * H + B);
+                }
+            T* tb = &wtab[((size_t)wl * nt + n) * nuv];
+            for (int k = 0; k < h.nu; ++k) tb[k] = T(expm1(h.u[k] * h.u[k] - lamw * (h.u[k] - Uw) * (h.u[k] - Uw)));
+            for (int k = 0; k < h.nv; ++k) tb[h.nu + k] = T(expm1(h.v[k] * h.v[k] - lamw * (h.v[k] - Vw) * (h.v[k] - Vw)));
+        }
+        double* oc = &oconst[wl * 8];
+        for (int jv = 0; jv < h.nv; ++jv)
+            for (int iu = 0; iu < h.nu; ++iu) {
+                const double u = h.u[iu], v = h.v[jv], w = h.wu[iu] * h.wv[jv];
+                const double un = ax == 0 ? u : v;
+                const double H = (1.0 / M_PI) * exp(-(u * u + v * v)), B = 0.5 * H;
+                const double f[4] = {un * H, un * u * H, un * v * H, un * 0.5 * ((u * u + v * v) * H + B)};
+                const int o = un * nin < 0 ? 0 : (un * nin > 0 ? 4 : -1);
+                if (o < 0) continue;
+                for (int k = 0; k < 4; ++k) oc[o + k] += w * f[k];
+            }
+    }
 }
 
 // host tables of one case uploaded into the workspace
@@ -304,6 +439,46 @@ cudaError_t upload_case(const HostCase& h, const CaseDev<T>& d, cudaStream_t s, 
     if ((e = put(d.v1, h.v.data(), sizeof(double) * h.nv))) return e;
     if ((e = put(d.wv1, h.wv.data(), sizeof(double) * h.nv))) return e;
     if ((e = put(d.refmom, &ref[0][0], sizeof ref))) return e;
+    // reference 1-D sums w x^p exp(-lam0 x^2) per node and over node subsets (all, positive, negative, zero)
+    std::vector<T> wxr((size_t)9 * h.nu), wyr((size_t)9 * h.nv);
+    std::vector<double> xr0(36, 0.0), yr0(36, 0.0);
+    std::vector<T> xr0t(36), yr0t(36);
+    for (int k = 0; k < h.nu; ++k) {
+        const double x = h.u[k], g = h.wu[k] * exp(-x * x);
+        const int row = x > 0 ? 1 : (x < 0 ? 2 : 3);
+        double pw = g;
+        for (int q = 0; q < 9; ++q) { wxr[(size_t)q * h.nu + k] = T(pw); xr0[row * 9 + q] += pw; xr0[q] += pw; pw *= x; }
+    }
+    for (int k = 0; k < h.nv; ++k) {
+        const double y = h.v[k], g = h.wv[k] * exp(-y * y);
+        const int row = y > 0 ? 1 : (y < 0 ? 2 : 3);
+        double pw = g;
+        for (int q = 0; q < 9; ++q) { wyr[(size_t)q * h.nv + k] = T(pw); yr0[row * 9 + q] += pw; yr0[q] += pw; pw *= y; }
+    }
+    for (int k = 0; k < 36; ++k) { xr0t[k] = T(xr0[k]); yr0t[k] = T(yr0[k]); }
+    if ((e = put(d.wxr, wxr.data(), sizeof(T) * wxr.size()))) return e;
+    if ((e = put(d.wyr, wyr.data(), sizeof(T) * wyr.size()))) return e;
+    if ((e = put(d.xr0, xr0.data(), sizeof(double) * 36))) return e;
+    if ((e = put(d.yr0, yr0.data(), sizeof(double) * 36))) return e;
+    if ((e = put(d.xr0t, xr0t.data(), sizeof(T) * 36))) return e;
+    if ((e = put(d.yr0t, yr0t.data(), sizeof(T) * 36))) return e;
+    {
+        std::vector<double> wconst, oconst;
+        std::vector<T> wtab;
+        wall_constants<T>(h, wconst, oconst, wtab);
+        if ((e = put(d.wconst, wconst.data(), sizeof(double) * wconst.size()))) return e;
+        if ((e = put(d.oconst, oconst.data(), sizeof(double) * oconst.size()))) return e;
+        if ((e = put(d.wtab, wtab.data(), sizeof(T) * wtab.size()))) return e;
+    }
+    std::vector<T> tu1(h.nu), tv1(h.nv);
+    for (int i = 0; i < h.nu; ++i) tu1[i] = T(h.u[i]);
+    for (int j = 0; j < h.nv; ++j) tv1[j] = T(h.v[j]);
+    if ((e = put(d.tu1, tu1.data(), sizeof(T) * h.nu))) return e;
+    if ((e = put(d.tv1, tv1.data(), sizeof(T) * h.nv))) return e;
+    std::vector<int> iu(h.nvp, 0), iv(h.nvp, 0);
+    for (int a = 0; a < h.nvel; ++a) { iu[a] = a % h.nu; iv[a] = a / h.nu; }
+    if ((e = put(d.viu, iu.data(), sizeof(int) * h.nvp))) return e;
+    if ((e = put(d.viv, iv.data(), sizeof(int) * h.nvp))) return e;
     return cudaSuccess;
 }
 
@@ -329,24 +504,82 @@ __global__ void k_begin_call(CaseStatus* st, int ncases)
 }
 
 template <typename T>
-void enqueue_iteration(Impl<T>& im, int ncases, cudaStream_t s)
+void launch_k1(int shape, int total, size_t smem, Batch<T> b, cudaStream_t s)
 {
-    const int* off = im.d_off;
-    const int stride = ncases + 1;
-    if (im.tot[0]) k1_moments<T><<<im.tot[0], 256, 0, s>>>(Batch<T>{im.d_cases, ncases, off + 0 * stride});
-    if (im.tot[1]) k2_face_params<T><<<im.tot[1], 128, 0, s>>>(Batch<T>{im.d_cases, ncases, off + 1 * stride});
-    if (im.tot[2]) k3_macro<T><<<im.tot[2], K3_THREADS, 0, s>>>(Batch<T>{im.d_cases, ncases, off + 2 * stride});
-    for (size_t g = 0; g < im.nt_groups.size(); ++g) {
-        Batch<T> b{im.d_cases, ncases, off + (4 + g) * stride};
-        if (im.k4tot[g]) k4_micro<T><<<im.k4tot[g], 256, 0, s>>>(b);
+    if (shape == 0) k1_tile<T, 4, 4, 6><<<total, 256, smem, s>>>(b);
+    else k1_tile<T, 4, 4, 3><<<total, 256, smem, s>>>(b);
+}
+
+template <typename T>
+void launch_k4(int shape, int total, size_t smem, Batch<T> b, cudaStream_t s)
+{
+    switch (shape) {
+        case 0: k4_tile<T, 4, 4><<<total, 256, smem, s>>>(b); break;
+        case 1: k4_tile<T, 4, 2><<<total, 256, smem, s>>>(b); break;
+        default: k4_tile<T, 2, 2><<<total, 256, smem, s>>>(b); break;
     }
-    k5_finish<T><<<ncases, 32, 0, s>>>(im.d_cases, ncases, off + 2 * stride);
+}
+
+template <typename T>
+cudaError_t set_smem_attributes(const Impl<T>& im)
+{
+    for (auto& sp : im.specs) {
+        cudaError_t e = cudaSuccess;
+        if (sp.kind == 0)
+            e = sp.shape == 0 ? cudaFuncSetAttribute(k1_tile<T, 4, 4, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem)
+                              : cudaFuncSetAttribute(k1_tile<T, 4, 4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem);
+        if (sp.kind == 4) {
+            switch (sp.shape) {
+                case 0: e = cudaFuncSetAttribute(k4_tile<T, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem); break;
+                case 1: e = cudaFuncSetAttribute(k4_tile<T, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem); break;
+                default: e = cudaFuncSetAttribute(k4_tile<T, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem); break;
+            }
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Kernel kinds reported by the profiler: 0 face moments, 1 face parameters, 2 macro update (with the
+// equilibrium tables), 3 micro update, 4 residual.
+inline int profile_slot(int kind) { return kind == 0 ? 0 : kind == 1 ? 1 : (kind == 2 || kind == 3) ? 2 : 3; }
+
+// one iteration; with `ev` (2 events per kernel kind, 5 kinds) each kind is bracketed by an event pair
+template <typename T>
+void enqueue_iteration(Impl<T>& im, int ncases, cudaStream_t s, cudaEvent_t* ev = nullptr)
+{
+    const int stride = ncases + 1;
+    int open_slot = -1;
+    for (auto& sp : im.specs) {
+        if (sp.kind == 5 || sp.total == 0) continue;
+        const int slot = profile_slot(sp.kind);
+        if (ev && slot != open_slot) {
+            if (open_slot >= 0) cudaEventRecord(ev[2 * open_slot + 1], s);
+            cudaEventRecord(ev[2 * slot], s);
+            open_slot = slot;
+        }
+        Batch<T> b{im.d_cases, ncases, im.d_off + (size_t)sp.table * stride};
+        switch (sp.kind) {
+            case 0: launch_k1<T>(sp.shape, sp.total, sp.smem, b, s); break;
+            case 1: k2_face_params<T><<<sp.total, 128, 0, s>>>(b); break;
+            case 2: k3_macro<T><<<sp.total, K3_THREADS, 0, s>>>(b); break;
+            case 3: k_tables<T><<<sp.total, 128, 0, s>>>(b); break;
+            case 4: launch_k4<T>(sp.shape, sp.total, sp.smem, b, s); break;
+        }
+    }
+    if (ev) {
+        cudaEventRecord(ev[2 * open_slot + 1], s);
+        cudaEventRecord(ev[8], s);
+    }
+    k5_finish<T><<<ncases, 32, 0, s>>>(im.d_cases, ncases, im.d_off + (size_t)im.k3_table * stride);
+    if (ev) cudaEventRecord(ev[9], s);
 }
 
 template <typename T>
 void enqueue_steps(Impl<T>& im, int ncases, cudaStream_t s)
 {
-    if (im.tot[3]) k_steps<T><<<im.tot[3], 128, 0, s>>>(Batch<T>{im.d_cases, ncases, im.d_off + 3 * (ncases + 1)});
+    const LaunchSpec& sp = im.specs[im.steps_table];
+    if (sp.total) k_steps<T><<<sp.total, 128, 0, s>>>(Batch<T>{im.d_cases, ncases, im.d_off + (size_t)sp.table * (ncases + 1)});
 }
 
 hbugks_status begin(hbugks_t h)
@@ -385,11 +618,15 @@ template <typename T>
 hbugks_status do_create(hbugks_t h, Impl<T>& im, int ncases, const hbugks_case* cases)
 {
     plan(im, ncases, cases, h->ws);
+    for (auto& hc : im.hc)
+        if (hc.k4shape < 0) return HBUGKS_EINVAL;
+    HB_CK(set_smem_attributes(im));
     std::vector<std::vector<char>> keep;
     for (int k = 0; k < ncases; ++k) HB_CK(upload_case(im.hc[k], im.dc[k], h->s, keep));
     HB_CK(cudaMemcpyAsync(im.d_cases, im.dc.data(), sizeof(CaseDev<T>) * ncases, cudaMemcpyHostToDevice, h->s));
     HB_CK(cudaMemcpyAsync(im.d_off, im.off_host.data(), sizeof(int) * im.off_host.size(), cudaMemcpyHostToDevice, h->s));
     HB_CK(cudaMemsetAsync(im.d_tol, 0, sizeof(double), h->s));
+    HB_CK(cudaMemsetAsync(im.d_err, 0, sizeof(int), h->s));
     k_status_reset<<<(ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, ncases, -1, 1);
     for (int k = 0; k < ncases; ++k) {
         const CaseDev<T>& d = im.dc[k];
@@ -403,7 +640,7 @@ hbugks_status do_create(hbugks_t h, Impl<T>& im, int ncases, const hbugks_case* 
 }
 
 template <class F>
-hbugks_status dispatch(hbugks_t h, F&& fn)
+auto dispatch(hbugks_t h, F&& fn) -> decltype(fn(*h->d))
 {
     if (h->f) return fn(*h->f);
     return fn(*h->d);
@@ -490,6 +727,13 @@ hbugks_status hbugks_set_wall(hbugks_t h, int ci, int wall, const hbugks_wall* w
         if (rc) return rc;
         HB_CK(cudaMemcpyAsync((void*)im.dc[ci].wall, im.hc[ci].wall_tab.data(),
                               sizeof(double) * im.hc[ci].wall_tab.size(), cudaMemcpyHostToDevice, h->s));
+        using TT = std::remove_const_t<typename std::remove_pointer<decltype(im.dc[ci].tu)>::type>;
+        std::vector<double> wconst, oconst;
+        std::vector<TT> wtab;
+        wall_constants<TT>(im.hc[ci], wconst, oconst, wtab);
+        HB_CK(cudaMemcpyAsync((void*)im.dc[ci].wconst, wconst.data(), sizeof(double) * wconst.size(),
+                              cudaMemcpyHostToDevice, h->s));
+        HB_CK(cudaMemcpyAsync((void*)im.dc[ci].wtab, wtab.data(), sizeof(TT) * wtab.size(), cudaMemcpyHostToDevice, h->s));
         HB_CK(cudaStreamSynchronize(h->s));
         return end(h);
     });
@@ -627,6 +871,14 @@ hbugks_status hbugks_iterate(hbugks_t h, int max_iters, double tol_rho, int* ite
             HB_CK(cudaMemcpyAsync(st.data(), im.d_status, sizeof(CaseStatus) * h->ncases, cudaMemcpyDeviceToHost, h->s));
             HB_CK(cudaStreamSynchronize(h->s));
         }
+        int err = 0;
+        HB_CK(cudaMemcpyAsync(&err, im.d_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+        HB_CK(cudaStreamSynchronize(h->s));
+        if (err) {
+            HB_CK(cudaMemsetAsync(im.d_err, 0, sizeof(int), h->s));
+            end(h);
+            return HBUGKS_TIMEOUT;
+        }
         bool diverged = false, all = true;
         for (int k = 0; k < h->ncases; ++k) {
             if (iters_done) iters_done[k] = (int)st[k].iters_call;
@@ -710,11 +962,41 @@ long long hbugks_iteration_count(hbugks_t h, int ci)
     return st.iters;
 }
 
+hbugks_status hbugks_profile_kernels(hbugks_t h, int n, double* ms)
+{
+    if (!h || n < 1 || !ms) return HBUGKS_EINVAL;
+    return dispatch(h, [&](auto& im) -> hbugks_status {
+        hbugks_status rc = begin(h);
+        if (rc) return rc;
+        cudaEvent_t ev[10];
+        for (int k = 0; k < 10; ++k) HB_CK(cudaEventCreate(&ev[k]));
+        HB_CK(cudaMemsetAsync(im.d_tol, 0, sizeof(double), h->s));
+        k_begin_call<<<(h->ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, h->ncases);
+        double acc[5] = {0, 0, 0, 0, 0};
+        for (int it = 0; it < n; ++it) {
+            enqueue_iteration(im, h->ncases, h->s, ev);
+            HB_CK(cudaEventSynchronize(ev[9]));
+            for (int k = 0; k < 5; ++k) {
+                float t = 0.f;
+                HB_CK(cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]));
+                acc[k] += t;
+            }
+        }
+        for (int k = 0; k < 10; ++k) cudaEventDestroy(ev[k]);
+        for (int k = 0; k < 5; ++k) ms[k] = acc[k] / n;
+        return end(h);
+    });
+}
+
 int hbugks_launches_per_iteration(hbugks_t h)
 {
     if (!h) return -1;
-    int g = h->f ? (int)h->f->nt_groups.size() : (int)h->d->nt_groups.size();
-    return 4 + g;
+    return dispatch(h, [&](auto& im) -> int {
+        int n = 1;   // residual kernel
+        for (auto& sp : im.specs)
+            if (sp.kind != 5 && sp.total) ++n;
+        return n;
+    });
 }
 
 const char* hbugks_status_string(hbugks_status s)

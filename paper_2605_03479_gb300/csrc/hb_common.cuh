@@ -1,7 +1,7 @@
 // Shared device definitions of the GB300 HB-UGKS path.
 //
 // State layout (per case), velocity-blocked "delta form":
-//   dh[vb][cell][level][32]   dh = h - H_ref  (T = double or float),  same for db = b - B_ref
+//   dh[vb][level][cell][32]   dh = h - H_ref  (T = double or float),  same for db = b - B_ref
 // with vb the block of 32 consecutive discrete velocities (one warp lane per velocity), cell = j*nx + i and
 // H_ref = (lam0/pi) exp(-lam0 |u|^2), B_ref = H_ref / (2 lam0), the reduced Maxwellian at rest at T0
 // (lam0 = 1).  Every update is applied to the deviations, which is algebraically identical to the update of
@@ -18,21 +18,28 @@ constexpr int VB = 32;        // velocities per block (= warp width)
 constexpr int MAXNT = 15;     // N_H <= 7
 constexpr int NM = 23;        // face moments per (face, level)
 constexpr int NCM = 13;       // cell moments per (cell, level)
-constexpr int NP = 48;        // face parameters per (face, level)
-constexpr int NCP = 32;       // cell parameters per (cell, level)
+constexpr int NP = 44;        // face parameters per (face, level), 16-byte aligned blocks
+constexpr int NCP = 48;       // cell parameters per (cell, level)
 constexpr int RING = 4096;    // residual history slots per case
 constexpr int K3_THREADS = 128;
+constexpr int WCN = 18;       // per wall and level: Aw[13] (reflected-half raw moments, unit density), Dw, Gw[4]
 
-// face parameter slots
+// Face parameter slots of the micro flux (delta form).  For an interface velocity u = (u, v) with normal
+// component u_n, the Maxwellian part of the time-integrated flux divided by dG_f is
+//   h: C1' dH + H Q(u, v),   b: C1' dB + B (Q(u, v) + l0 + l1 u + l2 v)
+// where dH = H - H_ref = H_ref [(r - 1) + r (ex + ey + ex ey)] with the separable factors ex(u), ey(v) of the
+// face table, Q is the bivariate cubic C1' s (c.q)(2 lam |c|^2 - 4) + C2' (u_n P(a_n) + u_t P(a_t)) + C3' P(A)
+// (a_n = a^L for u_n > 0, a^R for u_n < 0) and the linear term is the b-part difference.
+// Cubic monomial order: 1, u, v, u^2, uv, v^2, u^3, u^2 v, u v^2, v^3.  Blocks start on multiples of 4.
 enum FP {
-    F_R = 0, F_RM1, F_DL, F_TLU, F_TLV, F_LU2, F_I2L, F_DI2L, F_U, F_V, F_TL, F_SQX, F_SQY,
-    F_AL = 13, F_AR = 17, F_AT = 21, F_A = 25, F_C = 29,
-    F_WR = 34, F_WRM1, F_WDL, F_WTLU, F_WTLV, F_WLU2, F_WI2L, F_WDI2L, F_NIN
+    F_QL = 0, F_QR = 12, F_LBL = 24, F_LBR = 28, F_RM1 = 32, F_R = 33, F_I2L = 34, F_DI2L = 35,
+    F_C1 = 36, F_C4 = 37, F_C5 = 38, F_NIN = 39, F_WRM1 = 40, F_WR = 41, F_WI2L = 42, F_WDI2L = 43
 };
-// cell parameter slots: equilibrium of W^k at 0..12, of W^{k+1} at 13..25, update coefficients 26..31
-enum CP { C_EQ0 = 0, C_EQ1 = 13, C_KSELF = 26, C_KE, C_KP1, C_KP0, C_KDX, C_KDY };
-// equilibrium sub-slots (same order as the first 13 face slots)
-enum EQ { E_R = 0, E_RM1, E_DL, E_TLU, E_TLV, E_LU2, E_I2L, E_DI2L, E_U, E_V, E_TL, E_SQX, E_SQY };
+// Cell parameter slots: equilibrium of W^k at 0..19, of W^{k+1} at 20..39 (each: r - 1, r, 1/(2 lam),
+// 1/(2 lam) - 1/(2 lam0), Shakhov cubic s (c.q)(2 lam |c|^2 - 4) [10] at 4, b-part linear term 2 s (c.q) [3]
+// at 16), update coefficients of Eq. fv_h at 40..45.
+enum CP { C_EQ0 = 0, C_EQ1 = 20, C_KSELF = 40, C_KE, C_KP1, C_KP0, C_KDX, C_KDY };
+enum EQ { E_RM1 = 0, E_R, E_I2L, E_DI2L, E_SH = 4, E_SHB = 16 };
 
 struct CaseStatus {
     int active;          // iterating in the current call
@@ -50,12 +57,19 @@ struct CaseDev {
     int face_step;
     double omega, mu0, w_vss, pr, cfl, gam, umax, vmax, lam0;
     double e[8];                       // e_d = (-1)^d / (2 sin(pi d / N_T)), d = 1..N_H
+    T et[8];                           // the same in the storage precision
     const double* wall;                // [4][nt][3]  U_w, V_w, T_w per level
     const double *xn, *yn, *xc, *yc, *hx, *hy, *rdx, *rdy;   // rdx[i] = 1/(xc[i+1]-xc[i])
     const double *vu, *vv, *vw;        // per padded velocity
     const T *tu, *tv, *tw, *thref;     // per padded velocity
     const double *u1, *wu1, *v1, *wv1; // 1-D grids
+    const T *tu1, *tv1;                // 1-D nodes in the storage precision
     const double* refmom;              // [5][13]: full, u>0, u<0, v>0, v<0 moments of (H_ref, B_ref)
+    const T *wxr, *wyr;                // [9][nu], [9][nv]: w x^p exp(-lam0 x^2) per 1-D node
+    const double *xr0, *yr0;           // [4][9]: sums of the above over all / positive / negative / zero nodes
+    const T *xr0t, *yr0t;              // the same in the storage precision
+    const double* wconst;              // [4][nt][WCN] reflected-half constants of each wall Maxwellian
+    const double* oconst;              // [4][8]: incident and reflected flux moments of (H_ref, B_ref) per wall
     T* dh[2];
     T* db[2];
     double* W[2];
@@ -63,6 +77,12 @@ struct CaseDev {
     double* fmom;                      // [nf][nt][NM]
     double* cmom;                      // [nc][nt][NCM]
     T* fpar;                           // [nf][nt][NP]
+    T* ftab;                           // [nf][nt][nu + nv]   expm1 factors of the interface Maxwellian
+    T* wtab;                           // [4][nt][nu + nv]  expm1 factors of each wall's Maxwellian
+    T* ctab;                           // [nc][nt][2][nu + nv] expm1 factors of the cell equilibria (W^k, W^{k+1})
+    const int* viu;                    // per padded velocity: u index (0 for padding)
+    const int* viv;                    // per padded velocity: v index
+    int shakhov;                       // Pr != 1
     double* fflux;                     // [nf][nt][4]
     T* cpar;                           // [nc][nt][NCP]
     double* rpart;                     // [k3 blocks][4]
@@ -70,6 +90,14 @@ struct CaseDev {
     double* stage;                     // conversion staging (>= nc * nvel_pad doubles)
     CaseStatus* st;
     const double* tol;                 // shared residual target of the handle
+    int* err;                          // device error word of the handle (1: a bounded wait expired)
+};
+
+template <typename T>
+struct Batch {
+    const CaseDev<T>* cases;
+    int ncases;
+    const int* off;   // block offsets per case for this kernel, ncases + 1 entries
 };
 
 // --------------------------------------------------------------------------------- small helpers
@@ -86,7 +114,50 @@ __device__ __forceinline__ int find_case(const int* off, int ncases, int blk)
 
 __device__ __forceinline__ size_t sidx(int nc, int nt, int vb, int c, int n, int lane)
 {
-    return ((((size_t)vb * nc + c) * nt + n) << 5) + lane;
+    return ((((size_t)vb * nt + n) * nc + c) << 5) + lane;
+}
+
+// ---------------------------------------------------------------- bulk copies (TMA) with an mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// arrive on the barrier and add `bytes` to the transaction count its current phase waits for
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16) completing on `bar`
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `phase` of `bar` with an iteration limit; on expiry record the failure in *err and return false.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, int* err)
+{
+    for (int it = 0; it < (1 << 24); ++it)
+        if (mbar_try_wait(bar, phase)) return true;
+    atomicExch(err, 1);
+    return false;
 }
 
 template <typename T> __device__ __forceinline__ T t_expm1(T x);
@@ -109,24 +180,24 @@ __device__ __forceinline__ double relax_time(double mu0, double w, double lam0, 
 }
 
 // Coefficients of Eq. C_coeffs: Taylor series in x = dG/tau below x = 1 (the printed forms cancel there),
-// printed forms with 1 - e^-x = -expm1(-x) above.
-__device__ __noinline__ void ugks_coeffs(double dG, double tau, double C[5])
+// printed forms with 1 - e^-x = -expm1(-x) above.  Evaluated in the precision P of their use.
+template <typename P>
+__device__ __noinline__ void ugks_coeffs(P dG, P tau, P C[5])
 {
-    double x = dG / tau;
-    if (x < 1.0) {
-        // terms t_j = x^j / j!, summed from the highest order down
-        double t[27];
-        t[0] = 1.0;
+    P x = dG / tau;
+    if (x < P(1)) {
+        P t[27];
+        t[0] = P(1);
 #pragma unroll
-        for (int j = 1; j <= 26; ++j) t[j] = t[j - 1] * x * (1.0 / j);
-        double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0;
+        for (int j = 1; j <= 26; ++j) t[j] = t[j - 1] * x * (P(1) / P(j));
+        P s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
 #pragma unroll
         for (int j = 26; j >= 1; --j) {
-            double sg = (j & 1) ? 1.0 : -1.0;
+            P sg = (j & 1) ? P(1) : P(-1);
             s4 += sg * t[j];
             if (j >= 2) s1 -= sg * t[j];
-            if (j >= 3) { s2 += sg * (2.0 - j) * t[j]; s3 += sg * t[j]; }
-            s5 += sg * (j - 1.0) * t[j];
+            if (j >= 3) { s2 += sg * P(2 - j) * t[j]; s3 += sg * t[j]; }
+            s5 += sg * P(j - 1) * t[j];
         }
         C[0] = tau * s1;
         C[1] = tau * tau * s2;
@@ -134,10 +205,10 @@ __device__ __noinline__ void ugks_coeffs(double dG, double tau, double C[5])
         C[3] = tau * s4;
         C[4] = tau * tau * s5;
     } else {
-        double phi = -expm1(-x), ex = exp(-x);
+        P phi = -t_expm1<P>(-x), ex = P(1) + t_expm1<P>(-x);
         C[0] = dG - tau * phi;
-        C[1] = 2.0 * tau * tau * phi - tau * dG - tau * dG * ex;
-        C[2] = 0.5 * dG * dG - tau * dG + tau * tau * phi;
+        C[1] = P(2) * tau * tau * phi - tau * dG - tau * dG * ex;
+        C[2] = P(0.5) * dG * dG - tau * dG + tau * tau * phi;
         C[3] = tau * phi;
         C[4] = tau * dG * ex - tau * tau * phi;
     }
@@ -156,139 +227,126 @@ __device__ __forceinline__ void micro_slope(const double w[4], double U, double 
     a[0] = w[0] - U * a[1] - V * a[2] - 0.5 * a[3] * e;
 }
 
-// Parameters of the delta-form equilibrium for the Maxwellian (rho, U, V, lam) with Shakhov heat flux q:
-// H - H_ref = H_ref [ r e^D - 1 ], D = (lam0 - lam)|u|^2 + 2 lam (uU + vV) - lam |U|^2, r = rho lam / lam0.
-__device__ inline void eq_params(double rho, double U, double V, double lam, double lam0, double pr,
-                                 double qx, double qy, double* o)
+// Shakhov factor s (c.q)(2 lam |c|^2 - 4), s = (1 - Pr) 4 lam^2 / (5 rho), c = u - U, as a cubic in (u, v)
+// (monomials 1, u, v, u^2, uv, v^2, u^3, u^2 v, u v^2, v^3), followed by the linear form 2 s (c.q) (1, u, v):
+// the reduced corrections are H+ = cubic * H and B+ = (cubic + linear) * B (Eq. shakhov integrated over xi).
+__device__ inline void shakhov_poly(double s, double qx, double qy, double U, double V, double lam, double* o)
 {
-    double r = rho * lam / lam0;
-    o[E_R] = r;
-    o[E_RM1] = r - 1.0;
-    o[E_DL] = lam0 - lam;
-    o[E_TLU] = 2.0 * lam * U;
-    o[E_TLV] = 2.0 * lam * V;
-    o[E_LU2] = lam * (U * U + V * V);
-    o[E_I2L] = 0.5 / lam;
-    o[E_DI2L] = 0.5 / lam - 0.5 / lam0;
-    o[E_U] = U;
-    o[E_V] = V;
-    o[E_TL] = 2.0 * lam;
-    // Shakhov (Eq. shakhov reduced over xi): H+ = s (c.q)(2 lam |c|^2 - 4) H, s = (1 - Pr) 4 lam^2 / (5 rho)
-    double s = (1.0 - pr) * 4.0 * lam * lam / (5.0 * rho);
-    o[E_SQX] = s * qx;
-    o[E_SQY] = s * qy;
+    const double a0 = -s * (qx * U + qy * V), a1 = s * qx, a2 = s * qy;      // s (c.q) = a0 + a1 u + a2 v
+    const double b3 = 2.0 * lam, b1 = -4.0 * lam * U, b2 = -4.0 * lam * V;
+    const double b0 = 2.0 * lam * (U * U + V * V) - 4.0;                       // 2 lam |c|^2 - 4
+    o[0] = a0 * b0;
+    o[1] = a0 * b1 + a1 * b0;
+    o[2] = a0 * b2 + a2 * b0;
+    o[3] = a0 * b3 + a1 * b1;
+    o[4] = a1 * b2 + a2 * b1;
+    o[5] = a0 * b3 + a2 * b2;
+    o[6] = a1 * b3;
+    o[7] = a2 * b3;
+    o[8] = a1 * b3;
+    o[9] = a2 * b3;
+    o[10] = 2.0 * a0;
+    o[11] = 2.0 * a1;
+    o[12] = 2.0 * a2;
 }
 
-// delta-form reduced equilibrium at one velocity: returns dH = H - H_ref, dB = B - B_ref and the Shakhov
-// corrections Hp, Bp, plus H itself (needed by the slope terms of the interface flux).
+// Cell equilibrium parameters (slots E_*) of the Maxwellian (rho, U, V, lam) with heat flux q
 template <typename T>
-__device__ __forceinline__ void eq_eval(const T* p, T u, T v, T u2, T href, T& H, T& dH, T& dB, T& Hp, T& Bp)
+__device__ inline void eq_cell(double rho, double U, double V, double lam, double lam0, double pr, double qx, double qy,
+                               T* o)
 {
-    T D = p[E_DL] * u2 + p[E_TLU] * u + p[E_TLV] * v - p[E_LU2];
-    T em1 = t_expm1<T>(D);
-    dH = href * (p[E_RM1] + p[E_R] * em1);
-    H = href + dH;
-    dB = dH * p[E_I2L] + href * p[E_DI2L];
-    T cx = u - p[E_U], cy = v - p[E_V];
-    T c2 = cx * cx + cy * cy;
-    T cq = p[E_SQX] * cx + p[E_SQY] * cy;
-    Hp = cq * (p[E_TL] * c2 - T(4)) * H;
-    Bp = cq * (p[E_TL] * c2 - T(2)) * (H * p[E_I2L]);
+    const double r = rho * lam / lam0;
+    o[E_RM1] = T(r - 1.0);
+    o[E_R] = T(r);
+    o[E_I2L] = T(0.5 / lam);
+    o[E_DI2L] = T(0.5 / lam - 0.5 / lam0);
+    double sp[13];
+    shakhov_poly((1.0 - pr) * 4.0 * lam * lam / (5.0 * rho), qx, qy, U, V, lam, sp);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) o[E_SH + k] = T(sp[k]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) o[E_SHB + k] = T(sp[10 + k]);
+}
+
+// Horner evaluation of the bivariate cubic with monomials 1, u, v, u^2, uv, v^2, u^3, u^2 v, u v^2, v^3
+template <typename T>
+__device__ __forceinline__ T cubic(const T* c, T u, T v)
+{
+    T yv = c[0] + v * (c[2] + v * (c[5] + v * c[9]));
+    T ux = (c[1] + v * (c[4] + v * c[8])) + u * ((c[3] + v * c[7]) + u * c[6]);
+    return yv + u * ux;
 }
 
 // ----------------------------------------------------------------------- analytic velocity sums
 // Discrete sums of polynomial x Maxwellian over the tensor velocity grid factor into 1-D sums
-//   X[p] = sum_i wu_i u_i^p exp(-lam (u_i - U)^2)  (restricted to u_i > 0, u_i < 0 or all),
+//   X[p] = sum_i wu_i u_i^p exp(-lam (u_i - U)^2)  (over u_i > 0, u_i < 0, u_i = 0 or all),
 //   Y[q] likewise in v,  so  sum_a w_a u^p v^q rho (lam/pi) e^{-lam |u - U|^2} = rho lam/pi X[p] Y[q].
 
-struct Sums1D {
-    double s[4][9];   // [0] all, [1] positive nodes, [2] negative nodes, [3] zero nodes; powers 0..8
+template <typename P>
+struct SumsT {
+    P s[4][9];   // [0] all, [1] positive nodes, [2] negative nodes, [3] zero nodes; powers 0..8
 };
 
-__device__ __noinline__ void sums1d(const double* x, const double* w, int n, double lam, double U, Sums1D& S)
-{
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int p = 0; p < 9; ++p) S.s[r][p] = 0.0;
-    for (int k = 0; k < n; ++k) {
-        double xv = x[k], d = xv - U;
-        double g = w[k] * exp(-lam * d * d);
-        int r = xv > 0.0 ? 1 : (xv < 0.0 ? 2 : 3);
-        double pw = g;
-#pragma unroll
-        for (int p = 0; p < 9; ++p) {
-            S.s[r][p] += pw;
-            pw *= xv;
-        }
-    }
-#pragma unroll
-    for (int p = 0; p < 9; ++p) S.s[0][p] = S.s[1][p] + S.s[2][p] + S.s[3][p];
-}
-
 // polynomial in (u, v) of total degree <= 4
-struct Poly {
-    double c[5][5];
+template <typename P>
+struct PolyT {
+    P c[5][5];
     __device__ void zero()
     {
 #pragma unroll
         for (int p = 0; p < 5; ++p)
 #pragma unroll
-            for (int q = 0; q < 5; ++q) c[p][q] = 0.0;
+            for (int q = 0; q < 5; ++q) c[p][q] = P(0);
     }
 };
 
-__device__ __noinline__ void poly_mul(const Poly& A, const Poly& B, Poly& C)
+template <typename P>
+__device__ __noinline__ void poly_mul(const PolyT<P>& A, const PolyT<P>& B, PolyT<P>& C)
 {
     C.zero();
-#pragma unroll
     for (int p = 0; p < 5; ++p)
-#pragma unroll
         for (int q = 0; q < 5 - p; ++q) {
-            double a = A.c[p][q];
-            if (a == 0.0) continue;
-#pragma unroll
+            const P a = A.c[p][q];
+            if (a == P(0)) continue;
             for (int r = 0; r < 5 - p; ++r)
-#pragma unroll
-                for (int s = 0; s < 5 - p - q - r; ++s)
-                    if (s >= 0) C.c[p + r][q + s] += a * B.c[r][s];
+                for (int s = 0; s < 5 - p - q - r; ++s) C.c[p + r][q + s] += a * B.c[r][s];
         }
 }
 
 // P_h(a) = a0 + a1 u + a2 v + a3/2 (u^2 + v^2 + 1/(2 lam)),  P_b(a) = P_h(a) + a3/(2 lam)
-__device__ inline void poly_P(const double* a, double i2l, bool for_b, Poly& P)
+template <typename P>
+__device__ inline void poly_P(const double* a, double i2l, bool for_b, PolyT<P>& out)
 {
-    P.zero();
-    P.c[0][0] = a[0] + 0.5 * a[3] * i2l + (for_b ? a[3] * i2l : 0.0);
-    P.c[1][0] = a[1];
-    P.c[0][1] = a[2];
-    P.c[2][0] = 0.5 * a[3];
-    P.c[0][2] = 0.5 * a[3];
+    out.zero();
+    out.c[0][0] = P(a[0] + 0.5 * a[3] * i2l + (for_b ? a[3] * i2l : 0.0));
+    out.c[1][0] = P(a[1]);
+    out.c[0][1] = P(a[2]);
+    out.c[2][0] = P(0.5 * a[3]);
+    out.c[0][2] = P(0.5 * a[3]);
 }
 
 // moments sum w psi [Q H ; R B] over the grid part selected by (rx, ry), H = pref e^{..}, B = H i2l:
 //   (sum Q H, sum u Q H, sum v Q H, 1/2 sum (|u|^2 Q H + R B))
-__device__ __noinline__ void mom4(const Poly& Q, const Poly& R, const Sums1D& X, int rx, const Sums1D& Y, int ry,
-                            double pref, double i2l, double out[4])
+template <typename P>
+__device__ __noinline__ void mom4(const PolyT<P>& Q, const PolyT<P>& R, const SumsT<P>& X, int rx, const SumsT<P>& Y,
+                                  int ry, P pref, P i2l, P out[4])
 {
-    double o0 = 0, o1 = 0, o2 = 0, o3 = 0, ob = 0;
-#pragma unroll
+    P o0 = 0, o1 = 0, o2 = 0, o3 = 0, ob = 0;
     for (int p = 0; p < 5; ++p)
-#pragma unroll
         for (int q = 0; q < 5 - p; ++q) {
-            double a = Q.c[p][q], r = R.c[p][q];
-            if (a != 0.0) {
+            const P a = Q.c[p][q], r = R.c[p][q];
+            if (a != P(0)) {
                 o0 += a * X.s[rx][p] * Y.s[ry][q];
                 o1 += a * X.s[rx][p + 1] * Y.s[ry][q];
                 o2 += a * X.s[rx][p] * Y.s[ry][q + 1];
                 o3 += a * (X.s[rx][p + 2] * Y.s[ry][q] + X.s[rx][p] * Y.s[ry][q + 2]);
             }
-            if (r != 0.0) ob += r * X.s[rx][p] * Y.s[ry][q];
+            if (r != P(0)) ob += r * X.s[rx][p] * Y.s[ry][q];
         }
     out[0] = pref * o0;
     out[1] = pref * o1;
     out[2] = pref * o2;
-    out[3] = 0.5 * pref * (o3 + i2l * ob);
+    out[3] = P(0.5) * pref * (o3 + i2l * ob);
 }
 
 }  // namespace hb

@@ -18,13 +18,6 @@
 
 namespace hb {
 
-template <typename T>
-struct Batch {
-    const CaseDev<T>* cases;
-    int ncases;
-    const int* off;   // block offsets per case for this kernel, ncases + 1 entries
-};
-
 // ------------------------------------------------------------------------------ geometry helpers
 
 struct FaceGeo {
@@ -55,201 +48,11 @@ __device__ __forceinline__ FaceGeo face_geo(const CaseDev<T>& cd, int f)
     return g;
 }
 
-// van Leer limited slope from backward / forward divided differences
-template <typename T>
-__device__ __forceinline__ T van_leer(T s1, T s2)
-{
-    T p = s1 * s2;
-    return p > T(0) ? T(2) * p / (s1 + s2) : T(0);
-}
-
-template <typename T>
-struct Rec {
-    T f, sx, sy;   // value and limited slopes of one array at one cell, level, velocity
-};
-
-// value and x / y slopes of array `a` at cell (i, j); a wall-adjacent cell uses its one-sided difference
-template <typename T>
-__device__ __forceinline__ Rec<T> rec(const CaseDev<T>& cd, const T* a, int vb, int i, int j, int n, int lane)
-{
-    const int nc = cd.nc, nt = cd.nt, nx = cd.nx, ny = cd.ny;
-    int c = j * nx + i;
-    Rec<T> r;
-    r.f = a[sidx(nc, nt, vb, c, n, lane)];
-    if (nx > 1) {
-        T s1 = 0, s2 = 0;
-        if (i > 0) s1 = (r.f - a[sidx(nc, nt, vb, c - 1, n, lane)]) * T(cd.rdx[i - 1]);
-        if (i < nx - 1) s2 = (a[sidx(nc, nt, vb, c + 1, n, lane)] - r.f) * T(cd.rdx[i]);
-        if (i == 0) s1 = s2;
-        if (i == nx - 1) s2 = s1;
-        r.sx = van_leer(s1, s2);
-    } else {
-        r.sx = 0;
-    }
-    if (ny > 1) {
-        T s1 = 0, s2 = 0;
-        if (j > 0) s1 = (r.f - a[sidx(nc, nt, vb, c - nx, n, lane)]) * T(cd.rdy[j - 1]);
-        if (j < ny - 1) s2 = (a[sidx(nc, nt, vb, c + nx, n, lane)] - r.f) * T(cd.rdy[j]);
-        if (j == 0) s1 = s2;
-        if (j == ny - 1) s2 = s1;
-        r.sy = van_leer(s1, s2);
-    } else {
-        r.sy = 0;
-    }
-    return r;
-}
-
-template <typename T>
-struct Up {
-    T d0, e0;      // reconstructed deviations of h and b at the face
-    T sn, st;      // normal / tangential slopes of h in the upwind cell
-    T snb, stb;    // same for b
-    int mode;      // 1: carried by the reconstruction (interior, or incident at a wall); 2: reflected at a
-                   // wall; 0: zero normal velocity at a wall
-};
-
-// Upwind reconstruction of (h, b) at face g for one velocity with normal component un (Sec 2.2)
-template <typename T>
-__device__ __forceinline__ Up<T> upwind(const CaseDev<T>& cd, const T* dh, const T* db, const FaceGeo& g, int vb,
-                                        int n, int lane, T un)
-{
-    Up<T> o;
-    const bool wall = !(g.hasL && g.hasR);
-    auto one = [&](bool left) {
-        int i = left ? g.iL : g.iR, j = left ? g.jL : g.jR;
-        Rec<T> rh = rec(cd, dh, vb, i, j, n, lane);
-        Rec<T> rb = rec(cd, db, vb, i, j, n, lane);
-        T off = g.axis == 0 ? T(left ? cd.hx[i] : -cd.hx[i]) : T(left ? cd.hy[j] : -cd.hy[j]);
-        Up<T> u;
-        if (g.axis == 0) {
-            u.sn = rh.sx; u.st = rh.sy; u.snb = rb.sx; u.stb = rb.sy;
-        } else {
-            u.sn = rh.sy; u.st = rh.sx; u.snb = rb.sy; u.stb = rb.sx;
-        }
-        u.d0 = rh.f + u.sn * off;
-        u.e0 = rb.f + u.snb * off;
-        u.mode = 1;
-        return u;
-    };
-    if (wall) {
-        bool left = g.hasL;                 // interior cell side
-        o = one(left);
-        T nin = left ? T(-1) : T(1);        // normal pointing into the fluid
-        T s = un * nin;
-        o.mode = s < T(0) ? 1 : (s > T(0) ? 2 : 0);
-        return o;
-    }
-    if (un > T(0)) return one(true);
-    if (un < T(0)) return one(false);
-    Up<T> a = one(true), b = one(false);
-    o.d0 = T(0.5) * (a.d0 + b.d0); o.e0 = T(0.5) * (a.e0 + b.e0);
-    o.sn = T(0.5) * (a.sn + b.sn); o.st = T(0.5) * (a.st + b.st);
-    o.snb = T(0.5) * (a.snb + b.snb); o.stb = T(0.5) * (a.stb + b.stb);
-    o.mode = 1;
-    return o;
-}
-
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
-}
-
-// ------------------------------------------------------------------------------ K1 face / cell moments
-
-template <typename T>
-__global__ void __launch_bounds__(256) k1_moments(Batch<T> B)
-{
-    int cs = find_case(B.off, B.ncases, blockIdx.x);
-    const CaseDev<T>& cd = B.cases[cs];
-    if (!cd.st->active) return;
-    const int lane = threadIdx.x & 31;
-    const int item = (blockIdx.x - B.off[cs]) * 8 + (threadIdx.x >> 5);
-    const int nt = cd.nt;
-    const int p = cd.st->parity;
-    const T* dh = cd.dh[p];
-    const T* db = cd.db[p];
-    if (item < cd.nf * nt) {
-        const int f = item / nt, n = item - f * nt;
-        const FaceGeo g = face_geo(cd, f);
-        T acc[NM];
-#pragma unroll
-        for (int k = 0; k < NM; ++k) acc[k] = T(0);
-        for (int vb = 0; vb < cd.nvb; ++vb) {
-            const int a = vb * VB + lane;
-            const T u = cd.tu[a], v = cd.tv[a], w = cd.tw[a];
-            const T un = g.axis == 0 ? u : v, ut = g.axis == 0 ? v : u;
-            Up<T> r = upwind(cd, dh, db, g, vb, n, lane, un);
-            const T u2 = u * u + v * v;
-            // tangential slopes: every velocity of the upwind / interior cell
-            acc[13] += w * r.st;
-            acc[14] += w * u * r.st;
-            acc[15] += w * v * r.st;
-            acc[16] += w * u2 * r.st;
-            acc[17] += w * r.stb;
-            if (r.mode == 1) {
-                const T wd = w * r.d0, we = w * r.e0;
-                acc[0] += wd;
-                acc[1] += wd * u;
-                acc[2] += wd * v;
-                acc[3] += wd * u * u;
-                acc[4] += wd * u * v;
-                acc[5] += wd * v * v;
-                acc[6] += wd * u * u * u;
-                acc[7] += wd * u * u * v;
-                acc[8] += wd * u * v * v;
-                acc[9] += wd * v * v * v;
-                acc[10] += we;
-                acc[11] += we * u;
-                acc[12] += we * v;
-                const T s = un * r.sn + ut * r.st, sb = un * r.snb + ut * r.stb;
-                const T wus = w * un * s;
-                acc[18] += wus;
-                acc[19] += wus * u;
-                acc[20] += wus * v;
-                acc[21] += wus * u2;
-                acc[22] += w * un * sb;
-            }
-        }
-        double* out = cd.fmom + (size_t)item * NM;
-#pragma unroll
-        for (int k = 0; k < NM; ++k) {
-            double s = warp_sum((double)acc[k]);
-            if (lane == 0) out[k] = s;
-        }
-    } else if (item < (cd.nf + cd.nc) * nt) {
-        const int it2 = item - cd.nf * nt;
-        const int c = it2 / nt, n = it2 - c * nt;
-        T acc[NCM];
-#pragma unroll
-        for (int k = 0; k < NCM; ++k) acc[k] = T(0);
-        for (int vb = 0; vb < cd.nvb; ++vb) {
-            const int a = vb * VB + lane;
-            const T u = cd.tu[a], v = cd.tv[a], w = cd.tw[a];
-            const size_t id = sidx(cd.nc, nt, vb, c, n, lane);
-            const T wd = w * dh[id], we = w * db[id];
-            acc[0] += wd;
-            acc[1] += wd * u;
-            acc[2] += wd * v;
-            acc[3] += wd * u * u;
-            acc[4] += wd * u * v;
-            acc[5] += wd * v * v;
-            acc[6] += wd * u * u * u;
-            acc[7] += wd * u * u * v;
-            acc[8] += wd * u * v * v;
-            acc[9] += wd * v * v * v;
-            acc[10] += we;
-            acc[11] += we * u;
-            acc[12] += we * v;
-        }
-        double* out = cd.cmom + (size_t)it2 * NCM;
-#pragma unroll
-        for (int k = 0; k < NCM; ++k) {
-            double s = warp_sum((double)acc[k]);
-            if (lane == 0) out[k] = s;
-        }
-    }
 }
 
 // heat flux from the 13 raw moments (h: 1,u,v,uu,uv,vv,uuu,uuv,uvv,vvv; b: 1,u,v) about (U, V):
@@ -266,6 +69,18 @@ __device__ __forceinline__ void heat_flux_raw(const double* A, double U, double 
 
 // ------------------------------------------------------------------------------ K2 face parameters
 
+// delta-form velocity sum sum_a w_a u^p v^q (H0 - H_ref) over the subset given by the rows (rx, ry), from the
+// reference 1-D sums X0, Y0 (FP64) and the table sums dX, dY = sum w x^p e^{-lam0 x^2} expm1(..):
+//   (lam0/pi) [(r - 1) X0 Y0 + r (dX Y0 + X0 dY + dX dY)]
+template <typename T>
+__device__ __forceinline__ double dsum(const double* X0, const double* Y0, const SumsT<T>& dX, const SumsT<T>& dY,
+                                       int rx, int ry, int p, int q, double r, double lam0)
+{
+    const double x0 = X0[rx * 9 + p], y0 = Y0[ry * 9 + q];
+    const double dx = (double)dX.s[rx][p], dy = (double)dY.s[ry][q];
+    return lam0 / M_PI * ((r - 1.0) * x0 * y0 + r * (dx * y0 + x0 * dy + dx * dy));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
 {
@@ -279,60 +94,36 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
     const FaceGeo g = face_geo(cd, f);
     const int p = cd.st->parity;
     const double* W = cd.W[p];
-    const double* m = cd.fmom + (size_t)item * NM;
+    const double* m = cd.fmom + (size_t)item * NM;     // velocity sums of the reconstructed deviations
     const bool wall = !(g.hasL && g.hasR);
     const double nin = wall ? (g.hasL ? -1.0 : 1.0) : 0.0;
     const int ax = g.axis;
-    // velocity-subset rows of the 1-D sums along the normal axis
     const int inc_row = nin > 0 ? 2 : 1;      // incident: u_n nin < 0
-    const int ref_row = nin > 0 ? 1 : 2;      // reflected: u_n nin > 0
     int refset = 0;
     if (wall) refset = ax == 0 ? (nin > 0 ? 2 : 1) : (nin > 0 ? 4 : 3);
     double A[13];
 #pragma unroll
     for (int k = 0; k < 13; ++k) A[k] = m[k] + cd.refmom[refset * 13 + k];
 
-    // ---- diffuse wall: Maxwellian of the wall, free-transport density estimate, mixed kinetic average
-    double Uw = 0, Vw = 0, lamw = 1, prefw = 0, i2lw = 0, Dw = 1, rhow0 = 0;
-    Sums1D Xw, Yw;
-    double Amix[13];
+    // ---- diffuse wall: free-transport density estimate (Eq. rho_wall) and the mixed kinetic average
+    const double* wc = wall ? cd.wconst + ((size_t)g.wall * nt + n) * WCN : nullptr;
+    double Amix[13], Dw = 1.0, rhow0 = 0.0;
 #pragma unroll
     for (int k = 0; k < 13; ++k) Amix[k] = A[k];
     if (wall) {
-        const double* ws = cd.wall + ((size_t)g.wall * nt + n) * 3;
-        Uw = ws[0]; Vw = ws[1]; lamw = cd.lam0 / ws[2];
-        sums1d(cd.u1, cd.wu1, cd.nu, lamw, Uw, Xw);
-        sums1d(cd.v1, cd.wv1, cd.nv, lamw, Vw, Yw);
-        prefw = lamw / M_PI;
-        i2lw = 0.5 / lamw;
-        const int rx = ax == 0 ? ref_row : 0, ry = ax == 0 ? 0 : ref_row;
-        double Aw[13];
-        Aw[0] = Xw.s[rx][0] * Yw.s[ry][0];
-        Aw[1] = Xw.s[rx][1] * Yw.s[ry][0];
-        Aw[2] = Xw.s[rx][0] * Yw.s[ry][1];
-        Aw[3] = Xw.s[rx][2] * Yw.s[ry][0];
-        Aw[4] = Xw.s[rx][1] * Yw.s[ry][1];
-        Aw[5] = Xw.s[rx][0] * Yw.s[ry][2];
-        Aw[6] = Xw.s[rx][3] * Yw.s[ry][0];
-        Aw[7] = Xw.s[rx][2] * Yw.s[ry][1];
-        Aw[8] = Xw.s[rx][1] * Yw.s[ry][2];
-        Aw[9] = Xw.s[rx][0] * Yw.s[ry][3];
+        Dw = wc[13];                                        // sum over reflected velocities of w |u_n| H_w
+        rhow0 = -nin * (ax == 0 ? A[1] : A[2]) / Dw;
 #pragma unroll
-        for (int k = 0; k < 10; ++k) Aw[k] *= prefw;
-        Aw[10] = i2lw * Aw[0]; Aw[11] = i2lw * Aw[1]; Aw[12] = i2lw * Aw[2];
-        Dw = nin * (ax == 0 ? Aw[1] : Aw[2]);                 // sum_refl w |u_n| H_w
-        rhow0 = -nin * (ax == 0 ? A[1] : A[2]) / Dw;          // Eq. rho_wall with the free-transport part
-#pragma unroll
-        for (int k = 0; k < 13; ++k) Amix[k] = A[k] + rhow0 * Aw[k];
+        for (int k = 0; k < 13; ++k) Amix[k] = A[k] + rhow0 * wc[k];
     }
 
     // ---- interface Maxwellian from the kinetic average, heat flux, relaxation time
     double W0[4] = {Amix[0], Amix[1], Amix[2], 0.5 * (Amix[3] + Amix[5] + Amix[10])};
-    double rho0, U0, V0, lam0f;
-    prim(W0, rho0, U0, V0, lam0f);
+    double rho0, U0, V0, lamf;
+    prim(W0, rho0, U0, V0, lamf);
     double q0x, q0y;
     heat_flux_raw(Amix, U0, V0, q0x, q0y);
-    const double tau = relax_time(cd.mu0, cd.w_vss, cd.lam0, rho0, lam0f);
+    const double tau = relax_time(cd.mu0, cd.w_vss, cd.lam0, rho0, lamf);
 
     // ---- face step (Eq. dt_face) and time-integration weights (Eq. C_coeffs)
     const int cL = g.jL * cd.nx + g.iL, cR = g.jR * cd.nx + g.iR;
@@ -341,24 +132,27 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
     else if (!g.hasR) dGf = cd.dG[cL];
     else if (cd.face_step == 1) dGf = 2.0 * cd.dG[cL] * cd.dG[cR] / (cd.dG[cL] + cd.dG[cR]);
     else dGf = fmin(cd.dG[cL], cd.dG[cR]);
+    T Ct[5];
+    ugks_coeffs<T>(T(dGf), T(tau), Ct);
     double C[5];
-    ugks_coeffs(dGf, tau, C);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) C[k] = (double)Ct[k];
 
-    // ---- equilibrium slopes
+    // ---- equilibrium slopes a^L, a^R (normal), a_t (tangential)
     double aL[4], aR[4], at[4], Aa[4], w[4];
     if (g.hasL) {
         const double* WL = W + ((size_t)n * cd.nc + cL) * 4;
-        double d = ax == 0 ? cd.hx[g.iL] : cd.hy[g.jL];
+        const double d = ax == 0 ? cd.hx[g.iL] : cd.hy[g.jL];
 #pragma unroll
         for (int k = 0; k < 4; ++k) w[k] = (W0[k] - WL[k]) / d / rho0;
-        micro_slope(w, U0, V0, lam0f, aL);
+        micro_slope(w, U0, V0, lamf, aL);
     }
     if (g.hasR) {
         const double* WR = W + ((size_t)n * cd.nc + cR) * 4;
-        double d = ax == 0 ? cd.hx[g.iR] : cd.hy[g.jR];
+        const double d = ax == 0 ? cd.hx[g.iR] : cd.hy[g.jR];
 #pragma unroll
         for (int k = 0; k < 4; ++k) w[k] = (WR[k] - W0[k]) / d / rho0;
-        micro_slope(w, U0, V0, lam0f, aR);
+        micro_slope(w, U0, V0, lamf, aR);
     }
     if (!g.hasL) {
 #pragma unroll
@@ -369,46 +163,80 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
         for (int k = 0; k < 4; ++k) aR[k] = aL[k];
     }
     w[0] = m[13] / rho0; w[1] = m[14] / rho0; w[2] = m[15] / rho0; w[3] = 0.5 * (m[16] + m[17]) / rho0;
-    micro_slope(w, U0, V0, lam0f, at);
+    micro_slope(w, U0, V0, lamf, at);
 
-    // ---- analytic velocity sums of polynomial x interface Maxwellian
-    Sums1D X, Y;
-    sums1d(cd.u1, cd.wu1, cd.nu, lam0f, U0, X);
-    sums1d(cd.v1, cd.wv1, cd.nv, lam0f, V0, Y);
-    const double pref = rho0 * lam0f / M_PI, i2l = 0.5 / lam0f;
+    // ---- separable table of the interface Maxwellian and its 1-D sums
+    const int nu = cd.nu, nv = cd.nv, nuv = nu + nv;
+    T* tb = cd.ftab + (size_t)item * nuv;
+    SumsT<T> dX, dY;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 9; ++q) { dX.s[r][q] = T(0); dY.s[r][q] = T(0); }
+    {
+        const T dl = T(cd.lam0 - lamf);
+        T tl = T(2.0 * lamf * U0), l2 = T(lamf * U0 * U0);
+        for (int k = 0; k < nu; ++k) {
+            const T x = cd.tu1[k];
+            const T e = t_expm1<T>(dl * x * x + tl * x - l2);
+            tb[k] = e;
+            const int row = x > T(0) ? 1 : (x < T(0) ? 2 : 3);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) dX.s[row][q] += cd.wxr[q * nu + k] * e;
+        }
+        tl = T(2.0 * lamf * V0);
+        l2 = T(lamf * V0 * V0);
+        for (int k = 0; k < nv; ++k) {
+            const T y = cd.tv1[k];
+            const T e = t_expm1<T>(dl * y * y + tl * y - l2);
+            tb[nu + k] = e;
+            const int row = y > T(0) ? 1 : (y < T(0) ? 2 : 3);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) dY.s[row][q] += cd.wyr[q * nv + k] * e;
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            dX.s[0][q] = dX.s[1][q] + dX.s[2][q] + dX.s[3][q];
+            dY.s[0][q] = dY.s[1][q] + dY.s[2][q] + dY.s[3][q];
+        }
+    }
+    // full 1-D sums of the interface Maxwellian (reference + table part)
+    SumsT<T> X, Y;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            X.s[r][q] = cd.xr0t[r * 9 + q] + dX.s[r][q];
+            Y.s[r][q] = cd.yr0t[r * 9 + q] + dY.s[r][q];
+        }
+    const T pref = T(rho0 * lamf / M_PI), i2l = T(0.5 / lamf);
     auto rows = [&](int r, int& rx, int& ry) { rx = ax == 0 ? r : 0; ry = ax == 0 ? 0 : r; };
-    Poly un, ut;
+    PolyT<T> un, ut;
     un.zero(); ut.zero();
-    if (ax == 0) { un.c[1][0] = 1.0; ut.c[0][1] = 1.0; } else { un.c[0][1] = 1.0; ut.c[1][0] = 1.0; }
-    Poly PhL, PbL, PhR, PbR, Pht, Pbt, t1, t2;
-    poly_P(aL, i2l, false, PhL); poly_P(aL, i2l, true, PbL);
-    poly_P(aR, i2l, false, PhR); poly_P(aR, i2l, true, PbR);
-    poly_P(at, i2l, false, Pht); poly_P(at, i2l, true, Pbt);
+    if (ax == 0) { un.c[1][0] = T(1); ut.c[0][1] = T(1); } else { un.c[0][1] = T(1); ut.c[1][0] = T(1); }
+    PolyT<T> PhL, PbL, PhR, PbR, Pht, Pbt, t1, t2;
+    poly_P<T>(aL, 0.5 / lamf, false, PhL); poly_P<T>(aL, 0.5 / lamf, true, PbL);
+    poly_P<T>(aR, 0.5 / lamf, false, PhR); poly_P<T>(aR, 0.5 / lamf, true, PbR);
+    poly_P<T>(at, 0.5 / lamf, false, Pht); poly_P<T>(at, 0.5 / lamf, true, Pbt);
     // Q_side = u_n P_h(a_side) + u_t P_h(a_t),  R_side likewise with P_b
-    Poly QL, RL, QR, RR, Q0, R0;
+    PolyT<T> QL, RL, QR, RR, Q0, R0;
     poly_mul(un, PhL, QL); poly_mul(ut, Pht, t1);
-#pragma unroll
-    for (int a = 0; a < 5; ++a)
-#pragma unroll
-        for (int b = 0; b < 5; ++b) QL.c[a][b] += t1.c[a][b];
     poly_mul(un, PbL, RL); poly_mul(ut, Pbt, t2);
-#pragma unroll
-    for (int a = 0; a < 5; ++a)
-#pragma unroll
-        for (int b = 0; b < 5; ++b) RL.c[a][b] += t2.c[a][b];
     poly_mul(un, PhR, QR);
     poly_mul(un, PbR, RR);
 #pragma unroll
     for (int a = 0; a < 5; ++a)
 #pragma unroll
         for (int b = 0; b < 5; ++b) {
+            QL.c[a][b] += t1.c[a][b];
+            RL.c[a][b] += t2.c[a][b];
             QR.c[a][b] += t1.c[a][b];
             RR.c[a][b] += t2.c[a][b];
-            Q0.c[a][b] = 0.5 * (QL.c[a][b] + QR.c[a][b]);
-            R0.c[a][b] = 0.5 * (RL.c[a][b] + RR.c[a][b]);
+            Q0.c[a][b] = T(0.5) * (QL.c[a][b] + QR.c[a][b]);
+            R0.c[a][b] = T(0.5) * (RL.c[a][b] + RR.c[a][b]);
         }
     // compatibility: moments of (A.psi) g0 = - moments of (u_n a_n + u_t a_t) g0
-    double M[4], tmp[4];
+    T M[4], tmp[4];
     int rx, ry;
     if (!wall) {
         rows(1, rx, ry); mom4(QL, RL, X, rx, Y, ry, pref, i2l, M);
@@ -422,29 +250,29 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
         mom4(QL, RL, X, 0, Y, 0, pref, i2l, M);
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) w[k] = -M[k] / rho0;
-    micro_slope(w, U0, V0, lam0f, Aa);
+    for (int k = 0; k < 4; ++k) w[k] = -(double)M[k] / rho0;
+    micro_slope(w, U0, V0, lamf, Aa);
 
-    // ---- macro flux: velocity moments of the time-integrated interface distribution (Eq. macro_flux)
-    // C1 term: u_n (1 + Shakhov) ; Shakhov factor s (c.q)(2 lam |c|^2 - 4) for h and (... - 2) for b
-    const double sk = (1.0 - cd.pr) * 4.0 * lam0f * lam0f / (5.0 * rho0);
-    Poly cq, c2, sh, sb, q1, r1;
-    cq.zero(); c2.zero();
-    cq.c[1][0] = sk * q0x; cq.c[0][1] = sk * q0y; cq.c[0][0] = -sk * (q0x * U0 + q0y * V0);
-    c2.c[2][0] = 2.0 * lam0f; c2.c[0][2] = 2.0 * lam0f; c2.c[1][0] = -4.0 * lam0f * U0;
-    c2.c[0][1] = -4.0 * lam0f * V0; c2.c[0][0] = 2.0 * lam0f * (U0 * U0 + V0 * V0);
-    c2.c[0][0] -= 4.0;
-    poly_mul(cq, c2, sh);                 // s (c.q)(2 lam |c|^2 - 4)
-    sb = sh;
-    sb.c[1][0] += 2.0 * cq.c[1][0]; sb.c[0][1] += 2.0 * cq.c[0][1]; sb.c[0][0] += 2.0 * cq.c[0][0];
-    sh.c[0][0] += 1.0; sb.c[0][0] += 1.0;
-    poly_mul(un, sh, q1); poly_mul(un, sb, r1);
+    // ---- macro flux deviation (Eq. macro_flux minus the flux of H_ref, which cancels in every cell balance)
+    // Shakhov factor s (c.q)(2 lam |c|^2 - 4) and the b-part addition 2 s (c.q)
+    double sp[13];
+    shakhov_poly((1.0 - cd.pr) * 4.0 * lamf * lamf / (5.0 * rho0), q0x, q0y, U0, V0, lamf, sp);
+    PolyT<T> shk, cq2, sb;
+    shk.zero(); cq2.zero();
+    shk.c[0][0] = T(sp[0]); shk.c[1][0] = T(sp[1]); shk.c[0][1] = T(sp[2]); shk.c[2][0] = T(sp[3]);
+    shk.c[1][1] = T(sp[4]); shk.c[0][2] = T(sp[5]); shk.c[3][0] = T(sp[6]); shk.c[2][1] = T(sp[7]);
+    shk.c[1][2] = T(sp[8]); shk.c[0][3] = T(sp[9]);
+    cq2.c[0][0] = T(sp[10]); cq2.c[1][0] = T(sp[11]); cq2.c[0][1] = T(sp[12]);
+    sb = shk;
+    sb.c[0][0] += cq2.c[0][0]; sb.c[1][0] += cq2.c[1][0]; sb.c[0][1] += cq2.c[0][1];
     const int half = wall ? inc_row : 0;  // velocities carried by the integral solution
-    double F1[4], F2[4], F3[4], F4[4], F5[4];
+    PolyT<T> q1, r1;
+    poly_mul(un, shk, q1); poly_mul(un, sb, r1);
+    T F1s[4], F2[4], F3[4];
     rows(half, rx, ry);
-    mom4(q1, r1, X, rx, Y, ry, pref, i2l, F1);
+    mom4(q1, r1, X, rx, Y, ry, pref, i2l, F1s);
     // C2 term: u_n (u_n P(a_bar) + u_t P(a_t)) with a_bar = a^L for u_n > 0, a^R for u_n < 0
-    Poly uQ, uR;
+    PolyT<T> uQ, uR;
     if (!wall) {
         poly_mul(un, QL, uQ); poly_mul(un, RL, uR);
         rows(1, rx, ry); mom4(uQ, uR, X, rx, Y, ry, pref, i2l, F2);
@@ -457,64 +285,129 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
         rows(inc_row, rx, ry); mom4(uQ, uR, X, rx, Y, ry, pref, i2l, F2);
     }
     // C3 term: u_n P(A)
-    Poly PhA, PbA;
-    poly_P(Aa, i2l, false, PhA); poly_P(Aa, i2l, true, PbA);
+    PolyT<T> PhA, PbA;
+    poly_P<T>(Aa, 0.5 / lamf, false, PhA); poly_P<T>(Aa, 0.5 / lamf, true, PbA);
     poly_mul(un, PhA, uQ); poly_mul(un, PbA, uR);
     rows(half, rx, ry);
     mom4(uQ, uR, X, rx, Y, ry, pref, i2l, F3);
-    // C4 term: u_n psi h_0 (reconstruction; incident velocities only at a wall)
-    if (ax == 0) { F4[0] = A[1]; F4[1] = A[3]; F4[2] = A[4]; F4[3] = 0.5 * (A[6] + A[8] + A[11]); }
-    else { F4[0] = A[2]; F4[1] = A[4]; F4[2] = A[5]; F4[3] = 0.5 * (A[7] + A[9] + A[12]); }
-    // C5 term: u_n (u_n sigma_n + u_t sigma_t) psi
+    // C1 term, Maxwellian part: moments of u_n psi (H0 - H_ref, B0 - B_ref), in FP64 from the reference sums
+    const double rr = rho0 * lamf / cd.lam0, i2ld = 0.5 / lamf, di2l = 0.5 / lamf - 0.5 / cd.lam0;
+    double dF1[4];
+    {
+        rows(half, rx, ry);
+        auto S = [&](int pp, int qq) { return dsum(cd.xr0, cd.yr0, dX, dY, rx, ry, pp, qq, rr, cd.lam0); };
+        auto Sr = [&](int pp, int qq) { return cd.lam0 / M_PI * cd.xr0[rx * 9 + pp] * cd.yr0[ry * 9 + qq]; };
+        if (ax == 0) {
+            const double s10 = S(1, 0);
+            dF1[0] = s10; dF1[1] = S(2, 0); dF1[2] = S(1, 1);
+            dF1[3] = 0.5 * (S(3, 0) + S(1, 2)) + 0.5 * (i2ld * s10 + di2l * Sr(1, 0));
+        } else {
+            const double s01 = S(0, 1);
+            dF1[0] = s01; dF1[1] = S(1, 1); dF1[2] = S(0, 2);
+            dF1[3] = 0.5 * (S(2, 1) + S(0, 3)) + 0.5 * (i2ld * s01 + di2l * Sr(0, 1));
+        }
+    }
+    // C4 term: u_n psi (h_0 - H_ref) (reconstruction; incident velocities only at a wall); C5 term
+    double F4[4], F5[4];
+    if (ax == 0) { F4[0] = m[1]; F4[1] = m[3]; F4[2] = m[4]; F4[3] = 0.5 * (m[6] + m[8] + m[11]); }
+    else { F4[0] = m[2]; F4[1] = m[4]; F4[2] = m[5]; F4[3] = 0.5 * (m[7] + m[9] + m[12]); }
     F5[0] = m[18]; F5[1] = m[19]; F5[2] = m[20]; F5[3] = 0.5 * (m[21] + m[22]);
     double I[4], F[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) I[k] = C[0] * F1[k] + C[1] * F2[k] + C[2] * F3[k] + C[3] * F4[k] + C[4] * F5[k];
+    for (int k = 0; k < 4; ++k)
+        I[k] = C[0] * (dF1[k] + (double)F1s[k]) + C[1] * (double)F2[k] + C[2] * (double)F3[k] + C[3] * F4[k] + C[4] * F5[k];
     double rhow = 0.0;
     if (!wall) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) F[k] = I[k] / dGf;
     } else {
-        // impermeability (Eq. rho_wall) with the time-integrated incident flux; reflected part rho_w H_w
-        rhow = -nin * I[0] / (dGf * Dw);
-        Poly one;
-        one.zero();
-        one.c[0][0] = 1.0;
-        Poly uu;
-        poly_mul(un, one, uu);
-        int wx = ax == 0 ? ref_row : 0, wy = ax == 0 ? 0 : ref_row;
-        mom4(uu, uu, Xw, wx, Yw, wy, prefw, i2lw, tmp);
+        // impermeability (Eq. rho_wall) with the time-integrated incident mass flux; reflected part rho_w H_w
+        const double* oc = cd.oconst + g.wall * 8;           // [0..3] incident flux of H_ref, [4..7] reflected
+        const double Iinc0 = dGf * oc[0] + I[0];
+        rhow = -nin * Iinc0 / (dGf * Dw);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) F[k] = I[k] / dGf + rhow * tmp[k];
+        for (int k = 0; k < 4; ++k) F[k] = I[k] / dGf + rhow * wc[14 + k] - oc[4 + k];
     }
     double* fo = cd.fflux + (size_t)item * 4;
 #pragma unroll
     for (int k = 0; k < 4; ++k) fo[k] = F[k];
 
-    // ---- parameters of the micro flux
+    // ---- parameters of the micro flux (delta form, divided by dG_f): for each upwind side the cubic
+    // Q = C1' s(c.q)(2 lam |c|^2 - 4) + C2' (u_n P_h(a_side) + u_t P_h(a_t)) + C3' P_h(A) and the linear b-part
+    // difference C1' 2 s (c.q) + C2' (u_n a_side,3 + u_t a_t,3)/(2 lam) + C3' A_3/(2 lam)
     T* pp = cd.fpar + (size_t)item * NP;
-    double e[13];
-    eq_params(rho0, U0, V0, lam0f, cd.lam0, cd.pr, q0x, q0y, e);
+    const T C1p = T(C[0] / dGf), C2p = T(C[1] / dGf), C3p = T(C[2] / dGf);
+    for (int side = 0; side < 2; ++side) {
+        const PolyT<T>& Qs = side == 0 ? QL : QR;
+        const PolyT<T>& Rs = side == 0 ? RL : RR;
+        PolyT<T> qf, lb;
 #pragma unroll
-    for (int k = 0; k < 13; ++k) pp[k] = T(e[k]);
+        for (int a = 0; a < 5; ++a)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        pp[F_AL + k] = T(aL[k]);
-        pp[F_AR + k] = T(aR[k]);
-        pp[F_AT + k] = T(at[k]);
-        pp[F_A + k] = T(Aa[k]);
+            for (int b = 0; b < 5; ++b) {
+                qf.c[a][b] = C1p * shk.c[a][b] + C2p * Qs.c[a][b] + C3p * PhA.c[a][b];
+                lb.c[a][b] = C1p * cq2.c[a][b] + C2p * (Rs.c[a][b] - Qs.c[a][b]) + C3p * (PbA.c[a][b] - PhA.c[a][b]);
+            }
+        T* q = pp + (side == 0 ? F_QL : F_QR);
+        q[0] = qf.c[0][0]; q[1] = qf.c[1][0]; q[2] = qf.c[0][1]; q[3] = qf.c[2][0]; q[4] = qf.c[1][1];
+        q[5] = qf.c[0][2]; q[6] = qf.c[3][0]; q[7] = qf.c[2][1]; q[8] = qf.c[1][2]; q[9] = qf.c[0][3];
+        T* l = pp + (side == 0 ? F_LBL : F_LBR);
+        l[0] = lb.c[0][0]; l[1] = lb.c[1][0]; l[2] = lb.c[0][1];
     }
-#pragma unroll
-    for (int k = 0; k < 5; ++k) pp[F_C + k] = T(C[k] / dGf);
-    if (wall) {
-        eq_params(rhow, Uw, Vw, lamw, cd.lam0, 1.0, 0.0, 0.0, e);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) pp[F_WR + k] = T(e[k]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) pp[F_WR + k] = T(0);
-    }
+    pp[F_RM1] = T(rr - 1.0);
+    pp[F_R] = T(rr);
+    pp[F_I2L] = T(i2ld);
+    pp[F_DI2L] = T(di2l);
+    pp[F_C1] = C1p;
+    pp[F_C4] = T(C[3] / dGf);
+    pp[F_C5] = T(C[4] / dGf);
     pp[F_NIN] = T(nin);
+    if (wall) {
+        const double* ws = cd.wall + ((size_t)g.wall * nt + n) * 3;
+        const double lamw = cd.lam0 / ws[2];
+        const double rw = rhow * lamw / cd.lam0;
+        pp[F_WRM1] = T(rw - 1.0);
+        pp[F_WR] = T(rw);
+        pp[F_WI2L] = T(0.5 / lamw);
+        pp[F_WDI2L] = T(0.5 / lamw - 0.5 / cd.lam0);
+    } else {
+        pp[F_WRM1] = pp[F_WR] = pp[F_WI2L] = pp[F_WDI2L] = T(0);
+    }
+}
+
+// ------------------------------------------------------------------------------ separable Maxwellian tables
+
+// Tables of expm1(lam0 x^2 - lam (x - U)^2) over the 1-D velocity nodes, so that for a Maxwellian of density
+// rho: H - H_ref = H_ref [(r - 1) + r (ex + ey + ex ey)], r = rho lam / lam0.  One warp per face-level (interface
+// and, at walls, reflected Maxwellian) or cell-level (W^k and W^{k+1}); lanes over the nodes.
+template <typename T>
+__device__ __forceinline__ void fill_table(T* dst, const T* x1, int n, double lam0, double lam, double U, int lane)
+{
+    const T dl = T(lam0 - lam), tl = T(2.0 * lam * U), lu2 = T(lam * U * U);
+    for (int k = lane; k < n; k += 32) {
+        const T x = x1[k];
+        dst[k] = t_expm1<T>(dl * x * x + tl * x - lu2);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_tables(Batch<T> B)
+{
+    const int cs = find_case(B.off, B.ncases, blockIdx.x);
+    const CaseDev<T>& cd = B.cases[cs];
+    if (!cd.st->active) return;
+    const int lane = threadIdx.x & 31;
+    const int item = (blockIdx.x - B.off[cs]) * 4 + (threadIdx.x >> 5);   // cell-level pair, c * nt + n
+    const int nt = cd.nt, nuv = cd.nu + cd.nv;
+    if (item >= cd.nc * nt) return;
+    const int p = cd.st->parity;
+    for (int e = 0; e < 2; ++e) {
+        double rho, U, V, lam;
+        prim((e == 0 ? cd.W[p] : cd.W[p ^ 1]) + ((size_t)(item % nt) * cd.nc + item / nt) * 4, rho, U, V, lam);
+        T* dst = cd.ctab + ((size_t)item * 2 + e) * nuv;
+        fill_table(dst, cd.tu1, cd.nu, cd.lam0, lam, U, lane);
+        fill_table(dst + cd.nu, cd.tv1, cd.nv, cd.lam0, lam, V, lane);
+    }
 }
 
 // ------------------------------------------------------------------------------ local pseudo-time step
@@ -603,12 +496,9 @@ __global__ void __launch_bounds__(K3_THREADS) k3_macro(Batch<T> B)
             heat_flux_raw(A, U0, V0, qx, qy);
             const double t0 = relax_time(cd.mu0, cd.w_vss, cd.lam0, r0, l0);
             const double t1 = relax_time(cd.mu0, cd.w_vss, cd.lam0, r1, l1);
-            double e0[13], e1[13];
-            eq_params(r0, U0, V0, l0, cd.lam0, cd.pr, qx, qy, e0);
-            eq_params(r1, U1, V1, l1, cd.lam0, cd.pr, qx, qy, e1);
             T* cp = cd.cpar + ((size_t)c * nt + n) * NCP;
-#pragma unroll
-            for (int k = 0; k < 13; ++k) { cp[C_EQ0 + k] = T(e0[k]); cp[C_EQ1 + k] = T(e1[k]); }
+            eq_cell(r0, U0, V0, l0, cd.lam0, cd.pr, qx, qy, cp + C_EQ0);
+            eq_cell(r1, U1, V1, l1, cd.lam0, cd.pr, qx, qy, cp + C_EQ1);
             const double D = 1.0 + 0.5 * dG / t1;
             cp[C_KSELF] = T((1.0 - 0.5 * dG / t0) / D);
             cp[C_KE] = T(dG * cd.omega / D);
@@ -633,104 +523,6 @@ __global__ void __launch_bounds__(K3_THREADS) k3_macro(Batch<T> B)
     if (threadIdx.x == 0)
 #pragma unroll
         for (int k = 0; k < 4; ++k) cd.rpart[lb * 4 + k] = red[0][k];
-}
-
-// ------------------------------------------------------------------------------ K4 micro update
-
-template <typename T>
-struct FluxOut {
-    T h, b;
-};
-
-// micro flux of one face at one velocity, delta form (Eq. micro_flux minus u_n H_ref)
-template <typename T>
-__device__ __forceinline__ FluxOut<T> micro_flux(const CaseDev<T>& cd, const T* dh, const T* db, int f, int n, int vb,
-                                                 int lane, T u, T v, T u2, T href)
-{
-    const FaceGeo g = face_geo(cd, f);
-    const T* fp = cd.fpar + ((size_t)f * cd.nt + n) * NP;
-    const T un = g.axis == 0 ? u : v, ut = g.axis == 0 ? v : u;
-    FluxOut<T> o;
-    Up<T> r = upwind(cd, dh, db, g, vb, n, lane, un);
-    if (r.mode == 1) {
-        T H, dH, dB, Hp, Bp;
-        eq_eval(fp, u, v, u2, href, H, dH, dB, Hp, Bp);
-        const T* ab = un > T(0) ? fp + F_AL : fp + F_AR;
-        const T* at = fp + F_AT;
-        const T* A = fp + F_A;
-        const T q = T(0.5) * (u2 + fp[F_I2L]);
-        const T Pa = ab[0] + ab[1] * u + ab[2] * v + ab[3] * q;
-        const T Pt = at[0] + at[1] * u + at[2] * v + at[3] * q;
-        const T PA = A[0] + A[1] * u + A[2] * v + A[3] * q;
-        const T C2 = fp[F_C + 1], C3 = fp[F_C + 2];
-        const T Ph = C2 * (un * Pa + ut * Pt) + C3 * PA;
-        const T Pb = Ph + (C2 * (un * ab[3] + ut * at[3]) + C3 * A[3]) * fp[F_I2L];
-        o.h = un * (fp[F_C] * (dH + Hp) + Ph * H + fp[F_C + 3] * r.d0 + fp[F_C + 4] * (un * r.sn + ut * r.st));
-        o.b = un * (fp[F_C] * (dB + Bp) + Pb * H * fp[F_I2L] + fp[F_C + 3] * r.e0 +
-                    fp[F_C + 4] * (un * r.snb + ut * r.stb));
-    } else if (r.mode == 2) {
-        const T* w = fp + F_WR;
-        T D = w[2] * u2 + w[3] * u + w[4] * v - w[5];
-        T dHw = href * (w[1] + w[0] * t_expm1<T>(D));
-        o.h = un * dHw;
-        o.b = un * (dHw * w[6] + href * w[7]);
-    } else {
-        o.h = T(0);
-        o.b = T(0);
-    }
-    return o;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k4_micro(Batch<T> B)
-{
-    int cs = find_case(B.off, B.ncases, blockIdx.x);
-    const CaseDev<T>& cd = B.cases[cs];
-    if (!cd.st->active) return;
-    const int lane = threadIdx.x & 31;
-    const int item = (blockIdx.x - B.off[cs]) * 8 + (threadIdx.x >> 5);
-    if (item >= cd.nc * cd.nvb) return;
-    const int c = item % cd.nc, vb = item / cd.nc;
-    const int i = c % cd.nx, j = c / cd.nx;
-    const int nc = cd.nc, nt = cd.nt, nh = cd.nh;
-    const int p = cd.st->parity;
-    const T* dh = cd.dh[p];
-    const T* db = cd.db[p];
-    T* oh = cd.dh[p ^ 1];
-    T* ob = cd.db[p ^ 1];
-    const int a = vb * VB + lane;
-    const T u = cd.tu[a], v = cd.tv[a], href = cd.thref[a];
-    const T u2 = u * u + v * v;
-    const int fL = j * (cd.nx + 1) + i, fR = fL + 1, fB = cd.nfx + j * cd.nx + i, fT = fB + cd.nx;
-    const T* hcell = dh + sidx(nc, nt, vb, c, 0, lane);     // level n at hcell[32 n]
-    const T* bcell = db + sidx(nc, nt, vb, c, 0, lane);
-#pragma unroll 1
-    for (int n = 0; n < nt; ++n) {
-        const T* cp = cd.cpar + ((size_t)c * nt + n) * NCP;
-        FluxOut<T> xl = micro_flux(cd, dh, db, fL, n, vb, lane, u, v, u2, href);
-        FluxOut<T> xr = micro_flux(cd, dh, db, fR, n, vb, lane, u, v, u2, href);
-        FluxOut<T> yb = micro_flux(cd, dh, db, fB, n, vb, lane, u, v, u2, href);
-        FluxOut<T> yt = micro_flux(cd, dh, db, fT, n, vb, lane, u, v, u2, href);
-        // spectral source (E dh)_n = sum_d e_d (dh_{n-d} - dh_{n+d})
-        T eh = T(0), eb = T(0);
-        for (int d = 1; d <= nh; ++d) {
-            int nm = n - d; if (nm < 0) nm += nt;
-            int np = n + d; if (np >= nt) np -= nt;
-            eh += T(cd.e[d]) * (hcell[nm * VB] - hcell[np * VB]);
-            eb += T(cd.e[d]) * (bcell[nm * VB] - bcell[np * VB]);
-        }
-        T H1, dH1, dB1, Hp1, Bp1, H0, dH0, dB0, Hp0, Bp0;
-        eq_eval(cp + C_EQ1, u, v, u2, href, H1, dH1, dB1, Hp1, Bp1);
-        eq_eval(cp + C_EQ0, u, v, u2, href, H0, dH0, dB0, Hp0, Bp0);
-        const T kdx = cp[C_KDX], kdy = cp[C_KDY];
-        const T h0 = hcell[n * VB], b0 = bcell[n * VB];
-        T nh_ = cp[C_KSELF] * h0 - kdx * (xr.h - xl.h) - kdy * (yt.h - yb.h) - cp[C_KE] * eh +
-                cp[C_KP1] * (dH1 + Hp1) + cp[C_KP0] * (dH0 + Hp0);
-        T nb_ = cp[C_KSELF] * b0 - kdx * (xr.b - xl.b) - kdy * (yt.b - yb.b) - cp[C_KE] * eb +
-                cp[C_KP1] * (dB1 + Bp1) + cp[C_KP0] * (dB0 + Bp0);
-        oh[sidx(nc, nt, vb, c, n, lane)] = nh_;
-        ob[sidx(nc, nt, vb, c, n, lane)] = nb_;
-    }
 }
 
 // ------------------------------------------------------------------------------ K5 residual / status

@@ -57,7 +57,8 @@ class Case(C.Structure):
 EXPORTED = ("hbugks_workspace_bytes", "hbugks_create", "hbugks_destroy", "hbugks_set_wall", "hbugks_init_uniform",
             "hbugks_set_state", "hbugks_get_state", "hbugks_iterate", "hbugks_set_active",
             "hbugks_residual_history", "hbugks_get_level_fields", "hbugks_get_harmonic", "hbugks_iteration_count",
-            "hbugks_status_string", "hbugks_enqueue_iterations", "hbugks_launches_per_iteration")
+            "hbugks_status_string", "hbugks_enqueue_iterations", "hbugks_profile_kernels",
+            "hbugks_launches_per_iteration")
 
 
 def lib():
@@ -90,6 +91,7 @@ def lib():
             L.hbugks_status_string.argtypes = [i]
             L.hbugks_status_string.restype = C.c_char_p
             L.hbugks_enqueue_iterations.argtypes = [vp, i]
+            L.hbugks_profile_kernels.argtypes = [vp, i, pd]
             L.hbugks_launches_per_iteration.argtypes = [vp]
             for name in EXPORTED:
                 if name not in ("hbugks_workspace_bytes", "hbugks_destroy", "hbugks_iteration_count",
@@ -218,6 +220,13 @@ class Solver:
 
     def iteration_count(self, case_index: int = 0) -> int:
         return int(lib().hbugks_iteration_count(self.h, case_index))
+
+    def profile_kernels(self, n: int):
+        """Average ms per iteration of (face moments, face parameters, macro update, micro update, residual),
+        from CUDA events around each launch on the stream the kernels run on."""
+        ms = np.zeros(5)
+        _check(lib().hbugks_profile_kernels(self.h, int(n), _dp(ms)), "hbugks_profile_kernels")
+        return ms
 
     def launches_per_iteration(self) -> int:
         return int(lib().hbugks_launches_per_iteration(self.h))
