@@ -258,8 +258,8 @@ __device__ __forceinline__ T wsum(T v)
 }
 
 // Staged region of one level: each region row is a run of consecutive cells, contiguous both in global memory
-// (cell-major within a level) and in shared memory, so it moves with one bulk copy.  region_bytes() sizes it,
-// stage_level() issues the copies (one thread) completing on `bar`.
+// (cell-major within a level) and in shared memory, so it moves with one bulk copy.  region_bytes() sizes the
+// region of one level block; row_seg() gives the copy of one row.
 template <typename T, int TX, int TY>
 __device__ __forceinline__ uint32_t region_bytes(const CaseDev<T>& cd, int i0, int j0)
 {
@@ -276,21 +276,22 @@ __device__ __forceinline__ uint32_t region_bytes(const CaseDev<T>& cd, int i0, i
     return bytes;
 }
 
+// Bulk copy of staged row r of one level block: global element offset within the level, shared element offset,
+// bytes; false if the row lies outside the domain.
 template <typename T, int TX, int TY>
-__device__ __forceinline__ void stage_level(const CaseDev<T>& cd, int i0, int j0, const T* level_src, T* dst,
-                                            uint64_t* bar)
+__device__ __forceinline__ bool row_seg(int nx, int ny, int i0, int j0, int r, size_t& goff, int& soff, uint32_t& bytes)
 {
     using S = Tile<TX, TY>;
-    for (int r = 0; r < TY + 4; ++r) {
-        const int j = j0 + r - 2;
-        if (j < 0 || j >= cd.ny) continue;
-        int c0 = S::clo(r), c1 = S::chi(r);
-        if (i0 + c0 < 0) c0 = -i0;
-        if (i0 + c1 > cd.nx) c1 = cd.nx - i0;
-        if (c1 <= c0) continue;
-        bulk_g2s(dst + (size_t)S::idx(c0, r - 2) * VB, level_src + ((size_t)j * cd.nx + i0 + c0) * VB,
-                 (uint32_t)((c1 - c0) * VB * sizeof(T)), bar);
-    }
+    const int j = j0 + r - 2;
+    if (j < 0 || j >= ny) return false;
+    int c0 = S::clo(r), c1 = S::chi(r);
+    if (i0 + c0 < 0) c0 = -i0;
+    if (i0 + c1 > nx) c1 = nx - i0;
+    if (c1 <= c0) return false;
+    goff = ((size_t)j * nx + i0 + c0) * VB;
+    soff = S::idx(c0, r - 2) * VB;
+    bytes = (uint32_t)((c1 - c0) * VB * sizeof(T));
+    return true;
 }
 
 __device__ __forceinline__ void mbar_setup(uint64_t* bars, int n)
@@ -340,20 +341,27 @@ __global__ void __launch_bounds__(256) k1_tile(Batch<T> B)
     const T* __restrict__ tv = cd.tv;
     const T* __restrict__ tw = cd.tw;
     int* err = cd.err;
+    const uint32_t rbytes = region_bytes<T, TX, TY>(cd, i0, j0);
+    // staged copies of chunk k (G velocity blocks of level n, h and b), issued by the lanes of warp 0
     auto issue = [&](int k) {
         const int vb0 = k * G;
-        const int gk = min(G, cd.nvb - vb0);
+        const int gk = min(G, nvb - vb0);
         T* dst = buf + (size_t)(k & 1) * G * 2 * blk;
-        mbar_arrive_expect(&bars[k & 1], (uint32_t)(2 * gk) * region_bytes<T, TX, TY>(cd, i0, j0));
-        for (int g = 0; g < gk; ++g) {
-            const size_t src = ((size_t)(vb0 + g) * nt + n) * nc * VB;
-            stage_level<T, TX, TY>(cd, i0, j0, gh + src, dst + (size_t)(2 * g) * blk, &bars[k & 1]);
-            stage_level<T, TX, TY>(cd, i0, j0, gb + src, dst + (size_t)(2 * g + 1) * blk, &bars[k & 1]);
+        if (lane == 0) mbar_arrive_expect(&bars[k & 1], (uint32_t)(2 * gk) * rbytes);
+        __syncwarp();
+        for (int q = lane; q < gk * 2 * (TY + 4); q += 32) {
+            const int r = q % (TY + 4), ga = q / (TY + 4);   // ga = 2 g + array
+            size_t goff;
+            int soff;
+            uint32_t bytes;
+            if (!row_seg<T, TX, TY>(nx, ny, i0, j0, r, goff, soff, bytes)) continue;
+            const size_t src = ((size_t)(vb0 + (ga >> 1)) * nt + n) * nc * VB + goff;
+            bulk_g2s(dst + (size_t)ga * blk + soff, ((ga & 1) ? gb : gh) + src, bytes, &bars[k & 1]);
         }
     };
-    if (threadIdx.x == 0) issue(0);
+    if (warp == 0) issue(0);
     for (int k = 0; k < nchunk; ++k) {
-        if (threadIdx.x == 0 && k + 1 < nchunk) issue(k + 1);
+        if (warp == 0 && k + 1 < nchunk) issue(k + 1);
         const int fail = !mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), err);
         if (__syncthreads_or(fail)) return;
         const T* cb = buf + (size_t)(k & 1) * G * 2 * blk;
@@ -494,12 +502,21 @@ __global__ void __launch_bounds__(256) k4_tile(Batch<T> B)
     TileGeo<T, TX, TY>* geo = reinterpret_cast<TileGeo<T, TX, TY>*>(fst + S::NF);
     mbar_setup(bar, 1);
     const int p = cd.st->parity;
-    if (threadIdx.x == 0) {
-        mbar_arrive_expect(bar, (uint32_t)(2 * nt) * region_bytes<T, TX, TY>(cd, i0, j0));
-        for (int n = 0; n < nt; ++n) {
-            const size_t src = ((size_t)vb * nt + n) * nc * VB;
-            stage_level<T, TX, TY>(cd, i0, j0, cd.dh[p] + src, sh + (size_t)n * blk, bar);
-            stage_level<T, TX, TY>(cd, i0, j0, cd.db[p] + src, sb + (size_t)n * blk, bar);
+    if (warp == 0) {
+        // staged copies of every level of h and b, issued by the lanes of warp 0
+        if (lane == 0) mbar_arrive_expect(bar, (uint32_t)(2 * nt) * region_bytes<T, TX, TY>(cd, i0, j0));
+        __syncwarp();
+        const T* gh = cd.dh[p];
+        const T* gb = cd.db[p];
+        for (int q = lane; q < 2 * nt * (TY + 4); q += 32) {
+            const int r = q % (TY + 4), na = q / (TY + 4);   // na = 2 n + array
+            size_t goff;
+            int soff;
+            uint32_t bytes;
+            if (!row_seg<T, TX, TY>(nx, ny, i0, j0, r, goff, soff, bytes)) continue;
+            const int n = na >> 1;
+            const size_t src = ((size_t)vb * nt + n) * nc * VB + goff;
+            bulk_g2s(((na & 1) ? sb : sh) + (size_t)n * blk + soff, ((na & 1) ? gb : gh) + src, bytes, bar);
         }
     }
     load_geo<T, TX, TY>(cd, i0, j0, *geo);
