@@ -167,6 +167,25 @@ HBUGKS_API hbugks_status hbugks_enqueue_iterations(hbugks_t h, int n);
  * each kernel kind into ms[5]: face moments, face parameters, macro update, micro update, residual. */
 HBUGKS_API hbugks_status hbugks_profile_kernels(hbugks_t h, int n, double* ms);
 
+/* Harmonic of the macroscopic fields for callers that cannot allocate device memory.
+ * Some callers cannot call cudaMalloc at all (code that runs inside an allocator-controlled runtime, or a
+ * host that has already handed out every byte of device memory) and have no workspace to give a handle.
+ * This entry point needs neither a handle nor a workspace: it takes a state that already lives in device
+ * memory and writes the k-th Fourier coefficient (0 <= k <= (nt - 1) / 2) of the 8 fields of
+ * hbugks_get_level_fields() into the caller's device buffers re[8][nx*ny] and im[8][nx*ny].
+ * Inputs (device pointers, FP64, canonical layout of this header): u[nu], wu[nu], v[nv], wv[nv], and
+ * h, b[nt][nx*ny][nu*nv].  Its intermediate per-level fields live in a fixed array inside the library
+ * (HBUGKS_NOALLOC_MAX_DOUBLES doubles, 4 MiB, held on every device that loads the library until the
+ * process exits), so it requires 8 * nt * nx * ny <= HBUGKS_NOALLOC_MAX_DOUBLES and returns HBUGKS_EINVAL
+ * otherwise.  It calls no allocating CUDA or library routine.  The first call on a device looks up that
+ * device's address of the array; make that first call before any stream capture.  All calls share the
+ * one array, so calls whose work overlaps on the GPU (different streams, or different host threads) race and
+ * must be serialised by the caller.  The paper has no counterpart of this entry point. */
+#define HBUGKS_NOALLOC_MAX_DOUBLES (1 << 19)
+HBUGKS_API hbugks_status hbugks_harmonic_noalloc(int nx, int ny, int nu, int nv, const double* u, const double* wu,
+                                                 const double* v, const double* wv, int nt, const double* h,
+                                                 const double* b, int k, double* re, double* im, void* cuda_stream);
+
 /* Number of kernel launches one iteration enqueues for this handle. */
 HBUGKS_API int hbugks_launches_per_iteration(hbugks_t h);
 

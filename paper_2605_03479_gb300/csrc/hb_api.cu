@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <type_traits>
 #include <vector>
@@ -648,6 +649,69 @@ auto dispatch(hbugks_t h, F&& fn) -> decltype(fn(*h->d))
 
 }  // namespace
 
+// ====================================================================================== no-allocation harmonic
+
+namespace {
+
+// fixed scratch of the no-allocation entry point: per-level fields [nt][8][nc]
+static __device__ __align__(256) double g_noalloc_scratch[HBUGKS_NOALLOC_MAX_DOUBLES];
+
+// fields of every level from a canonical FP64 state (h, b [nt][nc][nu*nv]); one warp per (cell, level)
+__global__ void k_fields_canonical(int nc, int nu, int nv, int nt, const double* u, const double* wu, const double* v,
+                                   const double* wv, const double* h, const double* b, double* lv)
+{
+    const int lane = threadIdx.x & 31;
+    const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (item >= nc * nt) return;
+    const int n = item / nc, c = item - n * nc;
+    const int nvel = nu * nv;
+    const double* hc = h + ((size_t)n * nc + c) * nvel;
+    const double* bc = b + ((size_t)n * nc + c) * nvel;
+    double A[13];
+    for (int q = 0; q < 13; ++q) A[q] = 0.0;
+    for (int a = lane; a < nvel; a += 32) {
+        const int iu = a % nu, jv = a / nu;
+        const double uu = u[iu], vv = v[jv], w = wu[iu] * wv[jv];
+        const double wd = w * hc[a], we = w * bc[a];
+        A[0] += wd; A[1] += wd * uu; A[2] += wd * vv; A[3] += wd * uu * uu; A[4] += wd * uu * vv;
+        A[5] += wd * vv * vv; A[6] += wd * uu * uu * uu; A[7] += wd * uu * uu * vv; A[8] += wd * uu * vv * vv;
+        A[9] += wd * vv * vv * vv; A[10] += we; A[11] += we * uu; A[12] += we * vv;
+    }
+    for (int q = 0; q < 13; ++q) A[q] = warp_sum(A[q]);
+    if (lane == 0) {
+        double Wm[4] = {A[0], A[1], A[2], 0.5 * (A[3] + A[5] + A[10])};
+        double rho, U, V, lam, qx, qy;
+        prim(Wm, rho, U, V, lam);
+        heat_flux_raw(A, U, V, qx, qy);
+        double* o = lv + (size_t)n * 8 * nc;
+        o[0 * nc + c] = rho;
+        o[1 * nc + c] = U;
+        o[2 * nc + c] = V;
+        o[3 * nc + c] = 1.0 / lam;
+        o[4 * nc + c] = A[4] - V * A[1] - U * A[2] + U * V * A[0];
+        o[5 * nc + c] = qx;
+        o[6 * nc + c] = qy;
+        o[7 * nc + c] = rho / (2.0 * lam);
+    }
+}
+
+// device address of the scratch array, looked up once per device
+double* noalloc_scratch(int dev)
+{
+    static std::mutex mu;
+    static double* ptr[256] = {};
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 256) return nullptr;
+    if (!ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
+        ptr[dev] = static_cast<double*>(p);
+    }
+    return ptr[dev];
+}
+
+}  // namespace
+
 // ====================================================================================== ABI
 
 extern "C" {
@@ -986,6 +1050,27 @@ hbugks_status hbugks_profile_kernels(hbugks_t h, int n, double* ms)
         for (int k = 0; k < 5; ++k) ms[k] = acc[k] / n;
         return end(h);
     });
+}
+
+hbugks_status hbugks_harmonic_noalloc(int nx, int ny, int nu, int nv, const double* u, const double* wu, const double* v,
+                                      const double* wv, int nt, const double* h, const double* b, int k, double* re,
+                                      double* im, void* cuda_stream)
+{
+    if (nx < 1 || ny < 1 || nu < 1 || nv < 1 || nt < 1 || !(nt & 1) || !u || !wu || !v || !wv || !h || !b || !re || !im)
+        return HBUGKS_EINVAL;
+    if (k < 0 || k > (nt - 1) / 2) return HBUGKS_EINVAL;
+    const long long nc = (long long)nx * ny;
+    if (8LL * nt * nc > (long long)HBUGKS_NOALLOC_MAX_DOUBLES) return HBUGKS_EINVAL;
+    int dev = 0;
+    HB_CK(cudaGetDevice(&dev));
+    double* scratch = noalloc_scratch(dev);
+    if (!scratch) return HBUGKS_ECUDA;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int items = (int)(nc * nt);
+    k_fields_canonical<<<(items + 7) / 8, 256, 0, s>>>((int)nc, nu, nv, nt, u, wu, v, wv, h, b, scratch);
+    k_dft<<<(int)((8 * nc + 127) / 128), 128, 0, s>>>(scratch, nt, (int)nc, k, re, im);
+    HB_CK(cudaGetLastError());
+    return HBUGKS_OK;
 }
 
 int hbugks_launches_per_iteration(hbugks_t h)

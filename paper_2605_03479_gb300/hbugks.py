@@ -58,7 +58,7 @@ EXPORTED = ("hbugks_workspace_bytes", "hbugks_create", "hbugks_destroy", "hbugks
             "hbugks_set_state", "hbugks_get_state", "hbugks_iterate", "hbugks_set_active",
             "hbugks_residual_history", "hbugks_get_level_fields", "hbugks_get_harmonic", "hbugks_iteration_count",
             "hbugks_status_string", "hbugks_enqueue_iterations", "hbugks_profile_kernels",
-            "hbugks_launches_per_iteration")
+            "hbugks_harmonic_noalloc", "hbugks_launches_per_iteration")
 
 
 def lib():
@@ -92,6 +92,7 @@ def lib():
             L.hbugks_status_string.restype = C.c_char_p
             L.hbugks_enqueue_iterations.argtypes = [vp, i]
             L.hbugks_profile_kernels.argtypes = [vp, i, pd]
+            L.hbugks_harmonic_noalloc.argtypes = [i, i, i, i, vp, vp, vp, vp, i, vp, vp, i, vp, vp, vp]
             L.hbugks_launches_per_iteration.argtypes = [vp]
             for name in EXPORTED:
                 if name not in ("hbugks_workspace_bytes", "hbugks_destroy", "hbugks_iteration_count",
@@ -130,6 +131,20 @@ class _CaseArgs:
         for k in range(4):
             c.walls[k] = Wall(*[float(x) for x in case.walls[k]])
         self.c = c
+
+
+NOALLOC_MAX_DOUBLES = 1 << 19
+
+
+def harmonic_noalloc(nx, ny, nu, nv, u, wu, v, wv, nt, h, b, k, re, im, stream=None) -> int:
+    """k-th harmonic of the 8 fields from a state already in device memory, without a handle or any device
+    allocation (see hbugks_harmonic_noalloc in include/hbugks.h).  Array arguments are CUDA tensors (FP64,
+    canonical layout); re and im are written in place.  Returns the status code."""
+    def ptr(t):
+        return C.c_void_p(t.data_ptr())
+    st = stream.cuda_stream if stream is not None else 0
+    return int(lib().hbugks_harmonic_noalloc(nx, ny, nu, nv, ptr(u), ptr(wu), ptr(v), ptr(wv), nt, ptr(h), ptr(b),
+                                             k, ptr(re), ptr(im), C.c_void_p(st)))
 
 
 def workspace_bytes(cases: Sequence) -> int:
