@@ -13,7 +13,7 @@
 
 #include "hbugks.h"
 #include "hb_kernels.cuh"
-#include "hb_tiles.cuh"
+#include "hb_cells.cuh"
 
 using namespace hb;
 
@@ -56,34 +56,44 @@ struct HostCase {
     std::vector<double> xn, yn, u, wu, v, wv;
     double mu0, omega;
     std::vector<double> wall_tab;   // [4][nt][3]
+    // stored velocity order: sign classes 0 (u > 0, v > 0), 1 (u < 0, v > 0), 2 (u > 0, v < 0), 3 (u < 0, v < 0),
+    // each padded to whole blocks; per slot the canonical index jv * nu + iu (-1: padding) and the share of the
+    // node's weight (1/2 or 1/4 for a node with u = 0 or v = 0, stored in two or four classes)
+    std::vector<int> vcan, vcls;
+    std::vector<double> vfac;
     int k1b, k2b, k3b, k4b, ksb, ktb;
-    int k1shape, k4shape;
+    int k4shape;
 };
 
-// tile shapes of the tiled kernels: K4 (TX, TY), K1 (TX, TY, velocity blocks staged per pass)
+// K1 tile (TX x TY cells, one warp each) and velocity blocks staged per pass, per storage precision
+template <typename T> constexpr int K1_TX = 4;
+template <typename T> constexpr int K1_TY = std::is_same<T, float>::value ? 4 : 2;
+template <typename T> constexpr int K1_G = std::is_same<T, float>::value ? 8 : 6;
+
+template <typename T>
+constexpr size_t k1_smem_of()
+{
+    return k1_cells_smem<T, K1_TX<T>, K1_TY<T>, K1_G<T>>();
+}
+
+// K4 tile shapes (TX, TY, warps per CTA)
 struct Shape {
-    int tx, ty, g;
+    int tx, ty, nw;
 };
-constexpr Shape K4_SHAPES[] = {{4, 4, 0}, {4, 2, 0}, {2, 2, 0}};
+constexpr Shape K4_SHAPES[] = {{4, 4, 8}, {4, 2, 8}, {2, 2, 4}};
 constexpr int N_K4_SHAPES = 3;
-constexpr Shape K1_SHAPES[] = {{4, 4, 6}, {4, 4, 3}};
-constexpr int N_K1_SHAPES = 2;
 
 template <typename T>
 size_t k4_smem_of(int shape, int nt)
 {
     switch (shape) {
-        case 0: return k4_smem<T, 4, 4>(nt);
-        case 1: return k4_smem<T, 4, 2>(nt);
-        default: return k4_smem<T, 2, 2>(nt);
+        case 0: return k4_cells_smem<T, 4, 4>(nt);
+        case 1: return k4_cells_smem<T, 4, 2>(nt);
+        default: return k4_cells_smem<T, 2, 2>(nt);
     }
 }
 
-template <typename T>
-size_t k1_smem_of(int shape)
-{
-    return shape == 0 ? k1_smem<T, 4, 4, 6>() : k1_smem<T, 4, 4, 3>();
-}
+constexpr size_t SMEM_MAX = 226 * 1024;   // dynamic shared memory per CTA, leaving room for static
 
 // largest tile whose shared memory lets two CTAs share an SM, else the largest that fits at all
 template <typename T>
@@ -92,14 +102,8 @@ int pick_k4_shape(int nt)
     for (int s = 0; s < N_K4_SHAPES; ++s)
         if (k4_smem_of<T>(s, nt) <= 113 * 1024) return s;
     for (int s = 0; s < N_K4_SHAPES; ++s)
-        if (k4_smem_of<T>(s, nt) <= 227 * 1024) return s;
+        if (k4_smem_of<T>(s, nt) <= SMEM_MAX) return s;
     return -1;
-}
-
-template <typename T>
-int pick_k1_shape()
-{
-    return k1_smem_of<T>(0) <= 113 * 1024 ? 0 : 1;
 }
 
 bool validate(const hbugks_case& c)
@@ -132,8 +136,22 @@ void fill_host(HostCase& h, const hbugks_case& c)
     h.src = c;
     h.nx = c.mesh.nx; h.ny = c.mesh.ny; h.nu = c.vgrid.nu; h.nv = c.vgrid.nv;
     h.nvel = h.nu * h.nv;
-    h.nvb = (h.nvel + VB - 1) / VB;
-    h.nvp = h.nvb * VB;
+    h.vcan.clear(); h.vcls.clear(); h.vfac.clear();
+    for (int cls = 0; cls < 4; ++cls) {
+        const size_t first = h.vcan.size();
+        for (int jv = 0; jv < h.nv; ++jv)
+            for (int iu = 0; iu < h.nu; ++iu) {
+                const double uu = c.vgrid.u[iu], vv = c.vgrid.v[jv];
+                if ((cls & 1) ? uu > 0 : uu < 0) continue;
+                if ((cls & 2) ? vv > 0 : vv < 0) continue;
+                h.vcan.push_back(jv * h.nu + iu);
+                h.vfac.push_back((uu == 0 ? 0.5 : 1.0) * (vv == 0 ? 0.5 : 1.0));
+            }
+        while ((h.vcan.size() - first) % VB) { h.vcan.push_back(-1); h.vfac.push_back(0.0); }
+        for (size_t k = first; k < h.vcan.size(); k += VB) h.vcls.push_back(cls);
+    }
+    h.nvp = (int)h.vcan.size();
+    h.nvb = h.nvp / VB;
     h.nh = c.phys.n_harmonics;
     h.nt = 2 * h.nh + 1;
     h.nfx = h.ny * (h.nx + 1);
@@ -197,7 +215,7 @@ void layout_case(Carver& cv, const HostCase& h, CaseDev<T>& d)
         d.W[k] = cv.take<double>((size_t)h.nt * h.nc * 4);
     }
     d.dG = cv.take<double>(h.nc);
-    d.fmom = cv.take<double>((size_t)h.nf * h.nt * NM);
+    d.hmom = cv.take<double>((size_t)h.nc * h.nt * 4 * NM);
     d.cmom = cv.take<double>((size_t)h.nc * h.nt * NCM);
     d.fpar = cv.take<T>((size_t)h.nf * h.nt * NP);
     d.ftab = cv.take<T>((size_t)h.nf * h.nt * (h.nu + h.nv));
@@ -213,6 +231,8 @@ void layout_case(Carver& cv, const HostCase& h, CaseDev<T>& d)
     d.ctab = cv.take<T>((size_t)h.nc * h.nt * 2 * (h.nu + h.nv));
     d.viu = cv.take<int>(h.nvp);
     d.viv = cv.take<int>(h.nvp);
+    d.vcan = cv.take<int>(h.nvp);
+    d.vcls = cv.take<int>(h.nvb);
     d.shakhov = h.src.phys.pr != 1.0;
     d.fflux = cv.take<double>((size_t)h.nf * h.nt * 4);
     d.cpar = cv.take<T>((size_t)h.nc * h.nt * NCP);
@@ -267,6 +287,16 @@ struct hbugks_solver {
 namespace {
 
 template <typename T>
+void fill_offsets(Impl<T>& im, int ncases);
+
+void set_k4_blocks(HostCase& h)
+{
+    if (h.k4shape < 0) { h.k4b = 0; return; }
+    const Shape s4 = K4_SHAPES[h.k4shape];
+    h.k4b = ((h.nx + s4.tx - 1) / s4.tx) * ((h.ny + s4.ty - 1) / s4.ty) * h.nvb;
+}
+
+template <typename T>
 size_t plan(Impl<T>& im, int ncases, const hbugks_case* cases, char* base)
 {
     Carver cv{base};
@@ -275,11 +305,9 @@ size_t plan(Impl<T>& im, int ncases, const hbugks_case* cases, char* base)
     for (int k = 0; k < ncases; ++k) {
         HostCase& h = im.hc[k];
         fill_host(h, cases[k]);
-        h.k1shape = pick_k1_shape<T>();
         h.k4shape = pick_k4_shape<T>(h.nt);
-        const Shape s1 = K1_SHAPES[h.k1shape], s4 = K4_SHAPES[h.k4shape < 0 ? 0 : h.k4shape];
-        h.k1b = ((h.nx + s1.tx - 1) / s1.tx) * ((h.ny + s1.ty - 1) / s1.ty) * h.nt;
-        h.k4b = ((h.nx + s4.tx - 1) / s4.tx) * ((h.ny + s4.ty - 1) / s4.ty) * h.nvb;
+        h.k1b = ((h.nx + K1_TX<T> - 1) / K1_TX<T>) * ((h.ny + K1_TY<T> - 1) / K1_TY<T>) * h.nt;
+        set_k4_blocks(h);
     }
     im.d_cases = cv.take<CaseDev<T>>(ncases);
     im.d_status = cv.take<CaseStatus>(ncases);
@@ -288,16 +316,12 @@ size_t plan(Impl<T>& im, int ncases, const hbugks_case* cases, char* base)
     // launch specs: K1 per shape, K2, K3, tables, K4 per shape; plus the step kernel (state setting only)
     im.specs.clear();
     auto add = [&](int kind, int shape) { im.specs.push_back(LaunchSpec{kind, shape, (int)im.specs.size(), 0, 0}); };
-    for (int sh = 0; sh < N_K1_SHAPES; ++sh)
-        for (auto& h : im.hc)
-            if (h.k1shape == sh) { add(0, sh); break; }
+    add(0, 0);
     add(1, 0);
     add(2, 0);
     im.k3_table = (int)im.specs.size() - 1;
     add(3, 0);
-    for (int sh = 0; sh < N_K4_SHAPES; ++sh)
-        for (auto& h : im.hc)
-            if (h.k4shape == sh) { add(4, sh); break; }
+    for (int sh = 0; sh < N_K4_SHAPES; ++sh) add(4, sh);
     add(5, 0);
     im.steps_table = (int)im.specs.size() - 1;
     const int ntab = (int)im.specs.size();
@@ -308,6 +332,15 @@ size_t plan(Impl<T>& im, int ncases, const hbugks_case* cases, char* base)
         im.dc[k].tol = im.d_tol;
         im.dc[k].err = im.d_err;
     }
+    fill_offsets(im, ncases);
+    return cv.off + 256;
+}
+
+// block offset tables of every launch from the cases' block counts and K4 shapes
+template <typename T>
+void fill_offsets(Impl<T>& im, int ncases)
+{
+    const int ntab = (int)im.specs.size();
     im.off_host.assign((size_t)ntab * (ncases + 1), 0);
     for (auto& sp : im.specs) {
         int acc = 0;
@@ -317,7 +350,7 @@ size_t plan(Impl<T>& im, int ncases, const hbugks_case* cases, char* base)
             const HostCase& h = im.hc[k];
             int nb = 0;
             switch (sp.kind) {
-                case 0: if (h.k1shape == sp.shape) { nb = h.k1b; smem = std::max(smem, k1_smem_of<T>(sp.shape)); } break;
+                case 0: nb = h.k1b; smem = k1_smem_of<T>(); break;
                 case 1: nb = h.k2b; break;
                 case 2: nb = h.k3b; break;
                 case 3: nb = h.ktb; break;
@@ -330,7 +363,6 @@ size_t plan(Impl<T>& im, int ncases, const hbugks_case* cases, char* base)
         sp.total = acc;
         sp.smem = smem;
     }
-    return cv.off + 256;
 }
 
 // Constants of the diffuse walls, FP64 on the host (they depend only on the wall waveforms):
@@ -404,14 +436,21 @@ cudaError_t upload_case(const HostCase& h, const CaseDev<T>& d, cudaStream_t s, 
     std::vector<T> tu(h.nvp, T(0)), tv(h.nvp, T(0)), tw(h.nvp, T(0)), th(h.nvp, T(0));
     double ref[5][13];
     memset(ref, 0, sizeof ref);
+    std::vector<int> iu_(h.nvp, 0), iv_(h.nvp, 0);
+    for (int a = 0; a < h.nvp; ++a) {
+        const int can = h.vcan[a];
+        if (can < 0) continue;             // padding: zero velocity, weight and reference
+        const int iu = can % h.nu, jv = can / h.nu;
+        const double u = h.u[iu], v = h.v[jv], w = h.wu[iu] * h.wv[jv] * h.vfac[a];
+        vu[a] = u; vv[a] = v; vw[a] = w;
+        tu[a] = T(u); tv[a] = T(v); tw[a] = T(w); th[a] = T((1.0 / M_PI) * exp(-(u * u + v * v)));
+        iu_[a] = iu; iv_[a] = jv;
+    }
     for (int jv = 0; jv < h.nv; ++jv)
         for (int iu = 0; iu < h.nu; ++iu) {
-            int a = jv * h.nu + iu;
             double u = h.u[iu], v = h.v[jv], w = h.wu[iu] * h.wv[jv];
-            vu[a] = u; vv[a] = v; vw[a] = w;
             double href = (1.0 / M_PI) * exp(-(u * u + v * v));
             double bref = 0.5 * href;
-            tu[a] = T(u); tv[a] = T(v); tw[a] = T(w); th[a] = T(href);
             double m[13] = {href, u * href, v * href, u * u * href, u * v * href, v * v * href, u * u * u * href,
                             u * u * v * href, u * v * v * href, v * v * v * href, bref, u * bref, v * bref};
             bool in[5] = {true, u > 0, u < 0, v > 0, v < 0};
@@ -476,10 +515,10 @@ cudaError_t upload_case(const HostCase& h, const CaseDev<T>& d, cudaStream_t s, 
     for (int j = 0; j < h.nv; ++j) tv1[j] = T(h.v[j]);
     if ((e = put(d.tu1, tu1.data(), sizeof(T) * h.nu))) return e;
     if ((e = put(d.tv1, tv1.data(), sizeof(T) * h.nv))) return e;
-    std::vector<int> iu(h.nvp, 0), iv(h.nvp, 0);
-    for (int a = 0; a < h.nvel; ++a) { iu[a] = a % h.nu; iv[a] = a / h.nu; }
-    if ((e = put(d.viu, iu.data(), sizeof(int) * h.nvp))) return e;
-    if ((e = put(d.viv, iv.data(), sizeof(int) * h.nvp))) return e;
+    if ((e = put(d.viu, iu_.data(), sizeof(int) * h.nvp))) return e;
+    if ((e = put(d.viv, iv_.data(), sizeof(int) * h.nvp))) return e;
+    if ((e = put(d.vcan, h.vcan.data(), sizeof(int) * h.nvp))) return e;
+    if ((e = put(d.vcls, h.vcls.data(), sizeof(int) * h.nvb))) return e;
     return cudaSuccess;
 }
 
@@ -505,40 +544,32 @@ __global__ void k_begin_call(CaseStatus* st, int ncases)
 }
 
 template <typename T>
-void launch_k1(int shape, int total, size_t smem, Batch<T> b, cudaStream_t s)
+void launch_k1(int total, size_t smem, Batch<T> b, cudaStream_t s)
 {
-    if (shape == 0) k1_tile<T, 4, 4, 6><<<total, 256, smem, s>>>(b);
-    else k1_tile<T, 4, 4, 3><<<total, 256, smem, s>>>(b);
+    k1_cells<T, K1_TX<T>, K1_TY<T>, K1_G<T>><<<total, K1_TX<T> * K1_TY<T> * 32, smem, s>>>(b);
 }
 
 template <typename T>
 void launch_k4(int shape, int total, size_t smem, Batch<T> b, cudaStream_t s)
 {
     switch (shape) {
-        case 0: k4_tile<T, 4, 4><<<total, 256, smem, s>>>(b); break;
-        case 1: k4_tile<T, 4, 2><<<total, 256, smem, s>>>(b); break;
-        default: k4_tile<T, 2, 2><<<total, 256, smem, s>>>(b); break;
+        case 0: k4_cells<T, 4, 4, 8><<<total, 8 * 32, smem, s>>>(b); break;
+        case 1: k4_cells<T, 4, 2, 8><<<total, 8 * 32, smem, s>>>(b); break;
+        default: k4_cells<T, 2, 2, 4><<<total, 4 * 32, smem, s>>>(b); break;
     }
 }
 
+// every K4 shape may be chosen later (autotuning), so each gets the largest dynamic shared memory it can use
 template <typename T>
-cudaError_t set_smem_attributes(const Impl<T>& im)
+cudaError_t set_smem_attributes()
 {
-    for (auto& sp : im.specs) {
-        cudaError_t e = cudaSuccess;
-        if (sp.kind == 0)
-            e = sp.shape == 0 ? cudaFuncSetAttribute(k1_tile<T, 4, 4, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem)
-                              : cudaFuncSetAttribute(k1_tile<T, 4, 4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem);
-        if (sp.kind == 4) {
-            switch (sp.shape) {
-                case 0: e = cudaFuncSetAttribute(k4_tile<T, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem); break;
-                case 1: e = cudaFuncSetAttribute(k4_tile<T, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem); break;
-                default: e = cudaFuncSetAttribute(k4_tile<T, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sp.smem); break;
-            }
-        }
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    const int big = (int)SMEM_MAX;
+    cudaError_t e = cudaFuncSetAttribute(k1_cells<T, K1_TX<T>, K1_TY<T>, K1_G<T>>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k1_smem_of<T>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k4_cells<T, 4, 4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k4_cells<T, 4, 2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k4_cells<T, 2, 2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    return e;
 }
 
 // Kernel kinds reported by the profiler: 0 face moments, 1 face parameters, 2 macro update (with the
@@ -561,7 +592,7 @@ void enqueue_iteration(Impl<T>& im, int ncases, cudaStream_t s, cudaEvent_t* ev 
         }
         Batch<T> b{im.d_cases, ncases, im.d_off + (size_t)sp.table * stride};
         switch (sp.kind) {
-            case 0: launch_k1<T>(sp.shape, sp.total, sp.smem, b, s); break;
+            case 0: launch_k1<T>(sp.total, sp.smem, b, s); break;
             case 1: k2_face_params<T><<<sp.total, 128, 0, s>>>(b); break;
             case 2: k3_macro<T><<<sp.total, K3_THREADS, 0, s>>>(b); break;
             case 3: k_tables<T><<<sp.total, 128, 0, s>>>(b); break;
@@ -621,7 +652,7 @@ hbugks_status do_create(hbugks_t h, Impl<T>& im, int ncases, const hbugks_case* 
     plan(im, ncases, cases, h->ws);
     for (auto& hc : im.hc)
         if (hc.k4shape < 0) return HBUGKS_EINVAL;
-    HB_CK(set_smem_attributes(im));
+    HB_CK(set_smem_attributes<T>());
     std::vector<std::vector<char>> keep;
     for (int k = 0; k < ncases; ++k) HB_CK(upload_case(im.hc[k], im.dc[k], h->s, keep));
     HB_CK(cudaMemcpyAsync(im.d_cases, im.dc.data(), sizeof(CaseDev<T>) * ncases, cudaMemcpyHostToDevice, h->s));

@@ -1,0 +1,555 @@
+// Per-velocity kernels of one HB-UGKS iteration on sign-pure velocity blocks.
+//
+// The discrete velocities are stored in blocks of 32 (one warp lane each) in which u and v each keep one sign
+// (a zero node is stored once in each of the adjacent sign classes with its weight split between the copies).
+// The upwind side of every x-face is then the same for all lanes of a block, and so is that of every y-face,
+// so each cell reconstructs once per velocity block and the result serves the one x-face and the one y-face
+// lying downwind of it (Sec 2.2, upwind interface reconstruction):
+//   k1_cells : per (cell, level): velocity sums of the reconstruction of h^k at the cell's downwind faces,
+//              kept per sign class (half-face sums), and the raw moments of h^k;
+//   k4_cells : per (cell, level, 32 velocities): interface micro fluxes (Eq. micro_flux), spectral source and
+//              the semi-implicit collision update (Eq. fv_h).
+// A CTA of k1_cells owns a tile of cells and one level and runs over all velocity blocks; a CTA of k4_cells
+// owns a tile of cells and one velocity block and runs over all levels.  Both stage the tile and its halo in
+// shared memory with bulk copies (TMA) completing on an mbarrier.
+#pragma once
+#include "hb_common.cuh"
+
+namespace hb {
+
+template <typename T>
+__device__ __forceinline__ T vleer(T s1, T s2);
+template <>
+__device__ __forceinline__ double vleer<double>(double s1, double s2)
+{
+    double p = s1 * s2;
+    return p > 0.0 ? (p + p) / (s1 + s2) : 0.0;
+}
+// single precision: the limited slope needs no correctly rounded division (2-ulp reciprocal form)
+template <>
+__device__ __forceinline__ float vleer<float>(float s1, float s2)
+{
+    float p = s1 * s2;
+    return p > 0.f ? __fdividef(p + p, s1 + s2) : 0.f;
+}
+
+// van Leer slope of a cell from its two neighbours along one axis; a missing neighbour (wall) makes the
+// available one-sided difference the slope, a single cell along the axis has none
+template <typename T>
+__device__ __forceinline__ T slope(T fm, T f0, T fp, T wm, T wp, bool has_m, bool has_p, bool several)
+{
+    T s1 = (f0 - fm) * wm, s2 = (fp - f0) * wp;
+    if (!has_m) s1 = s2;
+    if (!has_p) s2 = s1;
+    return several ? vleer(s1, s2) : T(0);
+}
+
+// 16-byte read-only vector loads of N consecutive parameters (N a multiple of 16 / sizeof(T), p 16-byte aligned)
+template <int N>
+__device__ __forceinline__ void ldv(const float* p, float* o)
+{
+#pragma unroll
+    for (int k = 0; k < N; k += 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p + k));
+        o[k] = v.x; o[k + 1] = v.y; o[k + 2] = v.z; o[k + 3] = v.w;
+    }
+}
+template <int N>
+__device__ __forceinline__ void ldv(const double* p, double* o)
+{
+#pragma unroll
+    for (int k = 0; k < N; k += 2) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(p + k));
+        o[k] = v.x; o[k + 1] = v.y;
+    }
+}
+
+// spectral source of one cell and lane: sum_d e_d (f_{n-d} - f_{n+d}) for h and b (Eq. D_explicit in paired
+// form), levels lv elements apart in shared memory
+template <int NH, typename T>
+__device__ __forceinline__ void spectral(const T* hc, const T* bc, int n, int nt, int lv, const T* et, T& eh, T& eb)
+{
+    eh = T(0);
+    eb = T(0);
+#pragma unroll
+    for (int d = 1; d <= NH; ++d) {
+        int nm = n - d; nm += nm < 0 ? nt : 0;
+        int np = n + d; np -= np >= nt ? nt : 0;
+        eh += et[d] * (hc[nm * lv] - hc[np * lv]);
+        eb += et[d] * (bc[nm * lv] - bc[np * lv]);
+    }
+}
+
+__device__ __forceinline__ void mbar_setup(uint64_t* bars, int n)
+{
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < n; ++k) mbar_init(bars + k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+}
+
+__host__ __device__ constexpr size_t round16(size_t b) { return (b + 15) / 16 * 16; }
+
+// Sum over the 32 lanes of each of v[0..N-1] (N <= 32), recursive halving: after the step with distance d the
+// lanes with bit d set hold the upper half of the remaining values.  Returns, on lane l, the total of v[l]
+// (0 for l >= N).  v is destroyed.
+template <int N, typename T>
+__device__ __forceinline__ T lane_totals(T (&v)[N], int lane)
+{
+    T x[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) x[k] = k < N ? v[k] : T(0);
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        const bool hi = (lane & d) != 0;
+#pragma unroll
+        for (int k = 0; k < d; ++k) {
+            const T send = hi ? x[k] : x[k + d];
+            const T keep = hi ? x[k + d] : x[k];
+            x[k] = keep + __shfl_xor_sync(0xffffffffu, send, d);
+        }
+    }
+    return x[0];
+}
+
+// ------------------------------------------------------------------------------ K1: half-face sums
+
+// Velocity sums of one cell's reconstruction at its downwind faces.  Slots of the 23 sums (as for an
+// interface with normal n and tangent t, u_n = u.n):
+//   0..9   w d0 (1, u, v, u^2, uv, v^2, u^3, u^2 v, u v^2, v^3),  d0 the reconstructed h deviation at the face
+//   10..12 w e0 (1, u, v),                                         e0 the same for b
+//   13..16 w s_t (1, u, v, |u|^2), 17 w s_t^b                      tangential slopes of h and b
+//   18..21 w u_n (u_n s_n + u_t s_t) (1, u, v, |u|^2), 22 the same for b
+// A wall face takes 0..12 and 18..22 from the velocities moving into the wall only and 13..17 from all.
+// Half-face slots per (cell, level): 0 x-face of the u > 0 class (the right face), 1 u < 0 (left face),
+// 2 v > 0 (top face), 3 v < 0 (bottom face).
+template <typename T, int TX, int TY, int G>
+__global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
+{
+    constexpr int PX = TX + 2, PY = TY + 2, NR = PX * PY, NWC = TX * TY;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t bars[2];
+    __shared__ T sacc[NWC][4][NM];
+    const int cs = find_case(B.off, B.ncases, blockIdx.x);
+    const CaseDev<T>& cd = B.cases[cs];
+    if (!cd.st->active) return;
+    const int lb = blockIdx.x - B.off[cs];
+    const int ntx = (cd.nx + TX - 1) / TX, nty = (cd.ny + TY - 1) / TY;
+    const int tx = lb % ntx, ty = (lb / ntx) % nty, n = lb / (ntx * nty);
+    const int i0 = tx * TX, j0 = ty * TY;
+    const int nt = cd.nt, nc = cd.nc, nx = cd.nx, ny = cd.ny, nvb = cd.nvb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ti = warp % TX, tj = warp / TX, i = i0 + ti, j = j0 + tj;
+    const bool valid = i < nx && j < ny;
+    for (int k = lane; k < 4 * NM; k += 32) sacc[warp][k / NM][k % NM] = T(0);
+    mbar_setup(bars, 2);
+    // staged rectangle: columns i0-1 .. i0+TX, rows j0-1 .. j0+TY; buffers [2][G][h, b][NR][32]
+    constexpr size_t blk = (size_t)NR * VB;
+    T* buf = reinterpret_cast<T*>(smem_raw);
+    const int p = cd.st->parity;
+    const T* gh = cd.dh[p];
+    const T* gb = cd.db[p];
+    const int c0 = max(i0 - 1, 0), c1 = min(i0 + TX + 1, nx);
+    uint32_t rbytes = 0;
+    for (int r = 0; r < PY; ++r) {
+        const int jj = j0 - 1 + r;
+        if (jj >= 0 && jj < ny) rbytes += (uint32_t)((c1 - c0) * VB * sizeof(T));
+    }
+    const int nchunk = (nvb + G - 1) / G;
+    int* err = cd.err;
+    auto issue = [&](int k) {
+        const int vb0 = k * G, gk = min(G, nvb - vb0);
+        T* dst = buf + (size_t)(k & 1) * G * 2 * blk;
+        if (lane == 0) mbar_arrive_expect(&bars[k & 1], (uint32_t)(2 * gk) * rbytes);
+        __syncwarp();
+        for (int q = lane; q < gk * 2 * PY; q += 32) {
+            const int r = q % PY, ga = q / PY;   // ga = 2 g + array
+            const int jj = j0 - 1 + r;
+            if (jj < 0 || jj >= ny) continue;
+            const size_t src = ((size_t)(vb0 + (ga >> 1)) * nt + n) * nc * VB + ((size_t)jj * nx + c0) * VB;
+            bulk_g2s(dst + (size_t)ga * blk + (size_t)(r * PX + c0 - (i0 - 1)) * VB, ((ga & 1) ? gb : gh) + src,
+                     (uint32_t)((c1 - c0) * VB * sizeof(T)), &bars[k & 1]);
+        }
+    };
+    if (warp == 0) issue(0);
+
+    // the warp's cell: neighbours, spacings, half widths (uniform over the warp)
+    const bool hm = i > 0, hp = i < nx - 1, vm = j > 0, vp = j < ny - 1, sx = nx > 1, sy = ny > 1;
+    const T wxm = valid && hm ? T(cd.rdx[i - 1]) : T(0), wxp = valid && hp ? T(cd.rdx[i]) : T(0);
+    const T wym = valid && vm ? T(cd.rdy[j - 1]) : T(0), wyp = valid && vp ? T(cd.rdy[j]) : T(0);
+    const T hxh = valid ? T(cd.hx[i]) : T(0), hyh = valid ? T(cd.hy[j]) : T(0);
+    const int kc = (tj + 1) * PX + ti + 1;
+    const T* __restrict__ tu = cd.tu;
+    const T* __restrict__ tv = cd.tv;
+    const T* __restrict__ tw = cd.tw;
+    const int* __restrict__ vcls = cd.vcls;
+
+    T ax[NM], ay[NM], ac[NCM];
+#pragma unroll
+    for (int q = 0; q < NM; ++q) { ax[q] = T(0); ay[q] = T(0); }
+#pragma unroll
+    for (int q = 0; q < NCM; ++q) ac[q] = T(0);
+    int cur = -1;
+    // add the sums of the current sign class to its two half-face slots
+    auto flush = [&]() {
+        const T tx_ = lane_totals<NM>(ax, lane);
+        const T ty_ = lane_totals<NM>(ay, lane);
+        if (lane < NM) {
+            sacc[warp][(cur & 1) ? 1 : 0][lane] += tx_;
+            sacc[warp][(cur & 2) ? 3 : 2][lane] += ty_;
+        }
+#pragma unroll
+        for (int q = 0; q < NM; ++q) { ax[q] = T(0); ay[q] = T(0); }
+    };
+
+    for (int k = 0; k < nchunk; ++k) {
+        if (warp == 0 && k + 1 < nchunk) issue(k + 1);
+        const int fail = !mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), err);
+        if (__syncthreads_or(fail)) return;
+        const T* cb = buf + (size_t)(k & 1) * G * 2 * blk;
+        const int vb0 = k * G, gk = min(G, nvb - vb0);
+        if (valid) {
+            for (int g = 0; g < gk; ++g) {
+                const int cls = vcls[vb0 + g];
+                if (cls != cur) {
+                    if (cur >= 0) flush();
+                    cur = cls;
+                }
+                const int a = (vb0 + g) * VB + lane;
+                const T u = tu[a], v = tv[a], w = tw[a];
+                const T* ph = cb + (size_t)(2 * g) * blk + (size_t)kc * VB + lane;
+                const T* pb = ph + blk;
+                const T f0 = ph[0], g0 = pb[0];
+                const T sxh = slope(ph[-VB], f0, ph[VB], wxm, wxp, hm, hp, sx);
+                const T syh = slope(ph[-PX * VB], f0, ph[PX * VB], wym, wyp, vm, vp, sy);
+                const T sxb = slope(pb[-VB], g0, pb[VB], wxm, wxp, hm, hp, sx);
+                const T syb = slope(pb[-PX * VB], g0, pb[PX * VB], wym, wyp, vm, vp, sy);
+                const bool xn = (cls & 1) != 0, yn = (cls & 2) != 0;
+                const T offx = xn ? -hxh : hxh, offy = yn ? -hyh : hyh;
+                T d0x = f0 + sxh * offx, e0x = g0 + sxb * offx;
+                T d0y = f0 + syh * offy, e0y = g0 + syb * offy;
+                // a velocity parallel to a wall carries nothing into it
+                if ((xn ? !hm : !hp) && u == T(0)) { d0x = T(0); e0x = T(0); }
+                if ((yn ? !vm : !vp) && v == T(0)) { d0y = T(0); e0y = T(0); }
+                const T wu = w * u, wv = w * v, wuu = wu * u, wuv = wu * v, wvv = wv * v;
+                const T m[10] = {w, wu, wv, wuu, wuv, wvv, wuu * u, wuu * v, wvv * u, wvv * v};
+                const T wq = wuu + wvv;
+#pragma unroll
+                for (int q = 0; q < 10; ++q) {
+                    ax[q] += d0x * m[q];
+                    ay[q] += d0y * m[q];
+                    ac[q] += f0 * m[q];
+                }
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    ax[10 + q] += e0x * m[q];
+                    ay[10 + q] += e0y * m[q];
+                    ac[10 + q] += g0 * m[q];
+                }
+                ax[13] += syh * w; ax[14] += syh * wu; ax[15] += syh * wv; ax[16] += syh * wq; ax[17] += syb * w;
+                ay[13] += sxh * w; ay[14] += sxh * wu; ay[15] += sxh * wv; ay[16] += sxh * wq; ay[17] += sxb * w;
+                const T txh = u * (u * sxh + v * syh), tyh = v * (v * syh + u * sxh);
+                ax[18] += txh * w; ax[19] += txh * wu; ax[20] += txh * wv; ax[21] += txh * wq;
+                ay[18] += tyh * w; ay[19] += tyh * wu; ay[20] += tyh * wv; ay[21] += tyh * wq;
+                ax[22] += u * (u * sxb + v * syb) * w;
+                ay[22] += v * (v * syb + u * sxb) * w;
+            }
+        }
+        __syncthreads();
+    }
+    if (!valid) return;
+    if (cur >= 0) flush();
+    const T cm = lane_totals<NCM>(ac, lane);
+    __syncwarp();
+    const int c = j * nx + i;
+    if (lane < NCM) cd.cmom[((size_t)c * nt + n) * NCM + lane] = (double)cm;
+    double* hmo = cd.hmom + ((size_t)c * nt + n) * 4 * NM;
+    for (int k = lane; k < 4 * NM; k += 32) hmo[k] = (double)sacc[warp][k / NM][k % NM];
+}
+
+template <typename T, int TX, int TY, int G>
+constexpr size_t k1_cells_smem()
+{
+    return (size_t)2 * G * 2 * (TX + 2) * (TY + 2) * VB * sizeof(T);
+}
+
+// ------------------------------------------------------------------------------ K4: micro update
+
+// Micro flux (delta form, divided by dG_f) through the downwind face of the reconstructing cell, for one lane:
+// u_n [C1' dH + H Q + C4' d0 + C5' (u_n s_n + u_t s_t)] and the b counterpart, with the face's parameters fp
+// (cubic and linear terms of the upwind side `neg`: the high-side cell for u_n < 0) and expm1 factors tb.
+template <typename T>
+__device__ __forceinline__ void flux_down(const T* __restrict__ fp, const T* __restrict__ tb, int iu, int ivn, T href,
+                                          T u, T v, T un, T ut, bool neg, T d0, T e0, T sn, T st, T snb, T stb, T& Hf,
+                                          T& Bf)
+{
+    T sc[8];
+    ldv<8>(fp + F_RM1, sc);        // r - 1, r, 1/(2 lam), 1/(2 lam) - 1/(2 lam0), C1', C4', C5', nin
+    const T ex = __ldg(tb + iu), ey = __ldg(tb + ivn);
+    const T E = ex + ey + ex * ey;
+    const T dH = href * (sc[0] + sc[1] * E);
+    const T H = href + dH;
+    const T i2l = sc[2];
+    const T dB = dH * i2l + href * sc[3];
+    T q[12], l[4];
+    ldv<12>(fp + (neg ? F_QR : F_QL), q);
+    ldv<4>(fp + (neg ? F_LBR : F_LBL), l);
+    const T Q = cubic(q, u, v);
+    const T Qb = Q + l[0] + l[1] * u + l[2] * v;
+    Hf = un * (sc[4] * dH + H * Q + sc[5] * d0 + sc[6] * (un * sn + ut * st));
+    Bf = un * (sc[4] * dB + H * i2l * Qb + sc[5] * e0 + sc[6] * (un * snb + ut * stb));
+    if (un == T(0)) { Hf = T(0); Bf = T(0); }
+}
+
+// Flux (delta form, divided by dG_f) of the distribution a diffuse wall re-emits, rho_w H_w u_n: velocities of
+// the block leave the wall.
+template <typename T>
+__device__ __forceinline__ void flux_wall(const T* __restrict__ fp, const T* __restrict__ tb, int iu, int ivn, T href,
+                                          T un, T& Hf, T& Bf)
+{
+    T wp[4];
+    ldv<4>(fp + F_WRM1, wp);
+    const T ex = __ldg(tb + iu), ey = __ldg(tb + ivn);
+    const T E = ex + ey + ex * ey;
+    const T dHw = href * (wp[0] + wp[1] * E);
+    Hf = un * dHw;
+    Bf = un * (dHw * wp[2] + href * wp[3]);
+}
+
+// A CTA: a TX x TY tile of cells, one velocity block, all levels.  The staged rectangle holds the tile, two
+// cells of halo on the upwind side of each axis and one on the downwind side.  Per level, the first pass
+// reconstructs every tile cell and the upwind halo cells and evaluates the flux through each one's downwind
+// face (every face of the tile exactly once); the second pass applies Eq. fv_h to the tile cells.  The
+// second pass of level n runs together with the first pass of level n + 1 (the face fluxes are double
+// buffered), so one barrier separates the levels.
+template <typename T, int TX, int TY, int NW>
+__global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
+{
+    constexpr int PX = TX + 3, PY = TY + 3, NR = PX * PY;
+    constexpr int NCT = TX * TY, NFX = TY * (TX + 1), NFY = (TY + 1) * TX, NFT = NFX + NFY;
+    constexpr int NIT = NCT + TY + TX, NPASS = (NIT + NW - 1) / NW;
+    constexpr int lv = NR * VB;                               // one staged level of one array
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ uint64_t bar[1];
+    __shared__ T gxr[PX], gxh[PX], gyr[PY], gyh[PY];
+    const int cs = find_case(B.off, B.ncases, blockIdx.x);
+    const CaseDev<T>& cd = B.cases[cs];
+    if (!cd.st->active) return;
+    const int nvb = cd.nvb;
+    // velocity block fastest: the CTAs of one tile run together and share its face and cell parameters in L2
+    const int lb = blockIdx.x - B.off[cs];
+    const int vb = lb % nvb, tile = lb / nvb;
+    const int ntx = (cd.nx + TX - 1) / TX;
+    const int i0 = (tile % ntx) * TX, j0 = (tile / ntx) * TY;
+    const int nt = cd.nt, nc = cd.nc, nx = cd.nx, ny = cd.ny, nh = cd.nh, nfx = cd.nfx;
+    const int nuv = cd.nu + cd.nv;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cls = __ldg(cd.vcls + vb);
+    const bool xneg = (cls & 1) != 0, yneg = (cls & 2) != 0;
+    const int xlo = xneg ? -1 : -2, ylo = yneg ? -1 : -2;
+    const int iend = min(i0 + TX, nx), jend = min(j0 + TY, ny);
+    T* sh = reinterpret_cast<T*>(smem_raw);
+    T* sb = sh + nt * lv;
+    T* fbuf = sb + nt * lv;    // [level parity][h, b][NFT][32]
+    mbar_setup(bar, 1);
+    const int p = cd.st->parity;
+    const int c0 = max(i0 + xlo, 0), c1 = min(i0 + xlo + PX, nx);
+    if (warp == 0) {
+        uint32_t rb = 0;
+        for (int r = 0; r < PY; ++r) {
+            const int jj = j0 + ylo + r;
+            if (jj >= 0 && jj < ny && c1 > c0) rb += (uint32_t)((c1 - c0) * VB * sizeof(T));
+        }
+        if (lane == 0) mbar_arrive_expect(bar, (uint32_t)(2 * nt) * rb);
+        __syncwarp();
+        const T* gh = cd.dh[p];
+        const T* gb = cd.db[p];
+        for (int q = lane; q < 2 * nt * PY; q += 32) {
+            const int r = q % PY, na = q / PY;   // na = 2 n + array
+            const int jj = j0 + ylo + r;
+            if (jj < 0 || jj >= ny || c1 <= c0) continue;
+            const int n = na >> 1;
+            const size_t src = ((size_t)vb * nt + n) * nc * VB + ((size_t)jj * nx + c0) * VB;
+            bulk_g2s(((na & 1) ? sb : sh) + n * lv + (r * PX + c0 - (i0 + xlo)) * VB, ((na & 1) ? gb : gh) + src,
+                     (uint32_t)((c1 - c0) * VB * sizeof(T)), bar);
+        }
+    }
+    for (int k = threadIdx.x; k < PX; k += blockDim.x) {
+        const int ii = i0 + xlo + k;
+        gxr[k] = (ii >= 0 && ii < nx - 1) ? T(cd.rdx[ii]) : T(0);
+        gxh[k] = (ii >= 0 && ii < nx) ? T(cd.hx[ii]) : T(0);
+    }
+    for (int k = threadIdx.x; k < PY; k += blockDim.x) {
+        const int jj = j0 + ylo + k;
+        gyr[k] = (jj >= 0 && jj < ny - 1) ? T(cd.rdy[jj]) : T(0);
+        gyh[k] = (jj >= 0 && jj < ny) ? T(cd.hy[jj]) : T(0);
+    }
+    const int av = vb * VB + lane;
+    const T u = __ldg(cd.tu + av), v = __ldg(cd.tv + av), href = __ldg(cd.thref + av);
+    const int iu = __ldg(cd.viu + av), ivn = cd.nu + __ldg(cd.viv + av);
+    T et[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) et[d] = cd.et[d];
+    const T* __restrict__ fpar = cd.fpar;
+    const T* __restrict__ ftab = cd.ftab;
+    const T* __restrict__ wtab = cd.wtab;
+    const T* __restrict__ cpar = cd.cpar;
+    const T* __restrict__ ctab = cd.ctab;
+    const bool shakhov = cd.shakhov != 0;
+    const int NPf = nt * NP, NTf = nt * nuv;            // per-face strides of the face parameters and tables
+    const int fail = !mbar_wait(bar, 0u, cd.err);
+    if (__syncthreads_or(fail)) return;
+
+    for (int s = 0; s <= nt; ++s) {
+        if (s < nt) {
+            // ---- pass 1, level s: reconstruction and downwind-face fluxes
+            const int n = s;
+            T* Fh = fbuf + (n & 1) * 2 * NFT * VB + lane;
+            T* Fb = Fh + NFT * VB;
+            const T* fpn = fpar + n * NP;
+            const T* ftn = ftab + n * nuv;
+#pragma unroll
+            for (int r = 0; r < NPASS; ++r) {
+                const int it = warp + r * NW;
+                if (it >= NIT) break;
+                int ti, tj;
+                bool dox = true, doy = true;
+                if ((r + 1) * NW <= NCT || it < NCT) {
+                    ti = it % TX; tj = it / TX;
+                    if (i0 + ti >= nx || j0 + tj >= ny) continue;
+                } else if (it < NCT + TY) {
+                    tj = it - NCT; ti = xneg ? iend - i0 : -1; doy = false;
+                    if (j0 + tj >= ny) continue;
+                } else {
+                    ti = it - NCT - TY; tj = yneg ? jend - j0 : -1; dox = false;
+                    if (i0 + ti >= nx) continue;
+                }
+                const int i = i0 + ti, j = j0 + tj;
+                if (i < 0 || i >= nx || j < 0 || j >= ny) {
+                    // upwind face of the tile on a wall: the re-emitted distribution
+                    T Hf, Bf;
+                    int slot;
+                    if (dox) {
+                        const int fi = i < 0 ? 0 : nx, gface = j * (nx + 1) + fi;
+                        flux_wall(fpn + gface * NPf, wtab + ((i < 0 ? 3 : 1) * nt + n) * nuv, iu, ivn, href, u, Hf, Bf);
+                        slot = tj * (TX + 1) + fi - i0;
+                    } else {
+                        const int fj = j < 0 ? 0 : ny, gface = nfx + fj * nx + i;
+                        flux_wall(fpn + gface * NPf, wtab + ((j < 0 ? 0 : 2) * nt + n) * nuv, iu, ivn, href, v, Hf, Bf);
+                        slot = NFX + (fj - j0) * TX + ti;
+                    }
+                    Fh[slot * VB] = Hf;
+                    Fb[slot * VB] = Bf;
+                    continue;
+                }
+                const int kx = ti - xlo, ky = tj - ylo;
+                const T* ph = sh + n * lv + (ky * PX + kx) * VB + lane;
+                const T* pb = ph + nt * lv;
+                const T f0 = ph[0], g0 = pb[0];
+                const bool hm = i > 0, hp = i < nx - 1, vm = j > 0, vp = j < ny - 1;
+                const T wxm = gxr[kx - 1], wxp = gxr[kx], wym = gyr[ky - 1], wyp = gyr[ky];
+                const T sxh = slope(ph[-VB], f0, ph[VB], wxm, wxp, hm, hp, nx > 1);
+                const T sxb = slope(pb[-VB], g0, pb[VB], wxm, wxp, hm, hp, nx > 1);
+                const T syh = slope(ph[-PX * VB], f0, ph[PX * VB], wym, wyp, vm, vp, ny > 1);
+                const T syb = slope(pb[-PX * VB], g0, pb[PX * VB], wym, wyp, vm, vp, ny > 1);
+                if (dox) {
+                    const int fi = xneg ? i : i + 1, gface = j * (nx + 1) + fi;
+                    const T off = xneg ? -gxh[kx] : gxh[kx];
+                    T Hf, Bf;
+                    flux_down(fpn + gface * NPf, ftn + gface * NTf, iu, ivn, href, u, v, u, v, xneg, f0 + sxh * off,
+                              g0 + sxb * off, sxh, syh, sxb, syb, Hf, Bf);
+                    const int slot = tj * (TX + 1) + fi - i0;
+                    Fh[slot * VB] = Hf;
+                    Fb[slot * VB] = Bf;
+                }
+                if (doy) {
+                    const int fj = yneg ? j : j + 1, gface = nfx + fj * nx + i;
+                    const T off = yneg ? -gyh[ky] : gyh[ky];
+                    T Hf, Bf;
+                    flux_down(fpn + gface * NPf, ftn + gface * NTf, iu, ivn, href, u, v, v, u, yneg, f0 + syh * off,
+                              g0 + syb * off, syh, sxh, syb, sxb, Hf, Bf);
+                    const int slot = NFX + (fj - j0) * TX + ti;
+                    Fh[slot * VB] = Hf;
+                    Fb[slot * VB] = Bf;
+                }
+            }
+        }
+        if (s > 0) {
+            // ---- pass 2, level s - 1: Eq. fv_h with the spectral source (delta form)
+            const int n = s - 1;
+            const T* Fh = fbuf + (n & 1) * 2 * NFT * VB + lane;
+            const T* Fb = Fh + NFT * VB;
+            T* on = cd.dh[p ^ 1] + ((size_t)vb * nt + n) * nc * VB + lane;
+            T* onb = cd.db[p ^ 1] + ((size_t)vb * nt + n) * nc * VB + lane;
+            const T* cpn = cpar + n * NCP;
+            const T* ctn = ctab + n * 2 * nuv;
+#pragma unroll
+            for (int r = 0; r < (NCT + NW - 1) / NW; ++r) {
+                const int ct = warp + r * NW;
+                if (ct >= NCT) break;
+                const int ti = ct % TX, tj = ct / TX;
+                const int i = i0 + ti, j = j0 + tj;
+                if (i >= nx || j >= ny) continue;
+                const int c = j * nx + i;
+                const int fL = tj * (TX + 1) + ti, fB = NFX + tj * TX + ti;
+                const T dxh = Fh[(fL + 1) * VB] - Fh[fL * VB];
+                const T dyh = Fh[(fB + TX) * VB] - Fh[fB * VB];
+                const T dxb = Fb[(fL + 1) * VB] - Fb[fL * VB];
+                const T dyb = Fb[(fB + TX) * VB] - Fb[fB * VB];
+                const int kc = ((tj - ylo) * PX + ti - xlo) * VB + lane;
+                const T* hc = sh + kc;     // level m at hc[m * lv]
+                const T* bc = sb + kc;
+                T eh, eb;
+                switch (nh) {
+                    case 0: eh = T(0); eb = T(0); break;
+                    case 1: spectral<1>(hc, bc, n, nt, lv, et, eh, eb); break;
+                    case 2: spectral<2>(hc, bc, n, nt, lv, et, eh, eb); break;
+                    case 3: spectral<3>(hc, bc, n, nt, lv, et, eh, eb); break;
+                    case 4: spectral<4>(hc, bc, n, nt, lv, et, eh, eb); break;
+                    case 5: spectral<5>(hc, bc, n, nt, lv, et, eh, eb); break;
+                    case 6: spectral<6>(hc, bc, n, nt, lv, et, eh, eb); break;
+                    default: spectral<7>(hc, bc, n, nt, lv, et, eh, eb); break;
+                }
+                // equilibria of W^{k+1} (slot 1) and W^k (slot 0): dH = H - H_ref from the cell table, Shakhov cubic
+                const T* cp = cpn + c * nt * NCP;
+                const T* tb = ctn + c * nt * 2 * nuv;
+                T dhp[2], dbp[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    T q[20];
+                    ldv<20>(cp + (e == 0 ? C_EQ0 : C_EQ1), q);
+                    const T ex = __ldg(tb + e * nuv + iu), ey = __ldg(tb + e * nuv + ivn);
+                    const T E = ex + ey + ex * ey;
+                    const T dH = href * (q[E_RM1] + q[E_R] * E);
+                    const T dB = dH * q[E_I2L] + href * q[E_DI2L];
+                    if (shakhov) {
+                        const T H = href + dH;
+                        const T sk = cubic(q + E_SH, u, v);
+                        const T skb = sk + q[E_SHB] + q[E_SHB + 1] * u + q[E_SHB + 2] * v;
+                        dhp[e] = dH + H * sk;
+                        dbp[e] = dB + H * q[E_I2L] * skb;
+                    } else {
+                        dhp[e] = dH;
+                        dbp[e] = dB;
+                    }
+                }
+                T k[8];
+                ldv<8>(cp + C_KSELF, k);           // kself, kE, kp1, kp0, kdx, kdy
+                const T h0 = hc[n * lv], b0 = bc[n * lv];
+                on[c * VB] = k[0] * h0 - k[4] * dxh - k[5] * dyh - k[1] * eh + k[2] * dhp[1] + k[3] * dhp[0];
+                onb[c * VB] = k[0] * b0 - k[4] * dxb - k[5] * dyb - k[1] * eb + k[2] * dbp[1] + k[3] * dbp[0];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int TX, int TY>
+constexpr size_t k4_cells_smem(int nt)
+{
+    return round16(((size_t)2 * nt * (TX + 3) * (TY + 3) * VB + (size_t)2 * 2 * (TY * (TX + 1) + (TY + 1) * TX) * VB) *
+                   sizeof(T));
+}
+
+}  // namespace hb

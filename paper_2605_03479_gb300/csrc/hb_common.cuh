@@ -74,14 +74,16 @@ struct CaseDev {
     T* db[2];
     double* W[2];
     double* dG;
-    double* fmom;                      // [nf][nt][NM]
+    double* hmom;                      // [nc][nt][4][NM] half-face sums of the reconstruction per sign class
     double* cmom;                      // [nc][nt][NCM]
     T* fpar;                           // [nf][nt][NP]
     T* ftab;                           // [nf][nt][nu + nv]   expm1 factors of the interface Maxwellian
     T* wtab;                           // [4][nt][nu + nv]  expm1 factors of each wall's Maxwellian
     T* ctab;                           // [nc][nt][2][nu + nv] expm1 factors of the cell equilibria (W^k, W^{k+1})
-    const int* viu;                    // per padded velocity: u index (0 for padding)
-    const int* viv;                    // per padded velocity: v index
+    const int* viu;                    // per stored velocity: u index (0 for padding)
+    const int* viv;                    // per stored velocity: v index
+    const int* vcan;                   // per stored velocity: canonical index jv * nu + iu, -1 for padding
+    const int* vcls;                   // per velocity block: sign class (bit 0: u < 0, bit 1: v < 0)
     int shakhov;                       // Pr != 1
     double* fflux;                     // [nf][nt][4]
     T* cpar;                           // [nc][nt][NCP]

@@ -81,6 +81,27 @@ __device__ __forceinline__ double dsum(const double* X0, const double* Y0, const
     return lam0 / M_PI * ((r - 1.0) * x0 * y0 + r * (dx * y0 + x0 * dy + dx * dy));
 }
 
+// Velocity sums of the upwinded reconstruction at face g, level n, from the half-face sums of its cells: at an
+// interior face the low-side cell's u_n > 0 class plus the high-side cell's u_n < 0 class; at a wall the
+// interior cell's class moving into the wall, with the tangential-slope sums (13..17) over both classes.
+template <typename T>
+__device__ __forceinline__ void face_sums(const CaseDev<T>& cd, const FaceGeo& g, int n, double* m)
+{
+    const int sp = g.axis == 0 ? 0 : 2;                  // half-face slot of the u_n > 0 class, sp + 1: u_n < 0
+    const size_t stride = (size_t)cd.nt * 4 * NM;
+    const double* L = g.hasL ? cd.hmom + (size_t)(g.jL * cd.nx + g.iL) * stride + (size_t)n * 4 * NM : nullptr;
+    const double* R = g.hasR ? cd.hmom + (size_t)(g.jR * cd.nx + g.iR) * stride + (size_t)n * 4 * NM : nullptr;
+    if (g.hasL && g.hasR) {
+        for (int k = 0; k < NM; ++k) m[k] = L[sp * NM + k] + R[(sp + 1) * NM + k];
+    } else if (g.hasR) {
+        for (int k = 0; k < NM; ++k) m[k] = R[(sp + 1) * NM + k];
+        for (int k = 13; k < 18; ++k) m[k] += R[sp * NM + k];
+    } else {
+        for (int k = 0; k < NM; ++k) m[k] = L[sp * NM + k];
+        for (int k = 13; k < 18; ++k) m[k] += L[(sp + 1) * NM + k];
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
 {
@@ -94,7 +115,8 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
     const FaceGeo g = face_geo(cd, f);
     const int p = cd.st->parity;
     const double* W = cd.W[p];
-    const double* m = cd.fmom + (size_t)item * NM;     // velocity sums of the reconstructed deviations
+    double m[NM];                                        // velocity sums of the reconstructed deviations
+    face_sums(cd, g, n, m);
     const bool wall = !(g.hasL && g.hasR);
     const double nin = wall ? (g.hasL ? -1.0 : 1.0) : 0.0;
     const int ax = g.axis;
@@ -570,6 +592,14 @@ __global__ void k5_finish(const CaseDev<T>* cases, int ncases, const int* k3off)
 
 // ------------------------------------------------------------------------------ conversions and fields
 
+// sign class in which a node is stored first (classes in order 0..3: u > 0 first, then v > 0 first)
+template <typename T>
+__device__ __forceinline__ int first_class(const CaseDev<T>& cd, int can)
+{
+    const double u = cd.u1[can % cd.nu], v = cd.v1[can / cd.nu];
+    return (u < 0 ? 1 : 0) | (v < 0 ? 2 : 0);
+}
+
 // canonical FP64 level array (stage[c][a], a < nvel) -> delta-form internal layout of one level
 template <typename T>
 __global__ void k_set_level(CaseDev<T> cd, int n, int which, const double* stage)
@@ -582,10 +612,11 @@ __global__ void k_set_level(CaseDev<T> cd, int n, int which, const double* stage
     int c = r % cd.nc, vb = r / cd.nc;
     int a = vb * VB + lane;
     double val = 0.0;
-    if (a < cd.nvel) {
+    const int can = cd.vcan[a];
+    if (can >= 0) {
         double href = (cd.lam0 / M_PI) * exp(-cd.lam0 * (cd.vu[a] * cd.vu[a] + cd.vv[a] * cd.vv[a]));
         double rv = which == 0 ? href : href * 0.5 / cd.lam0;
-        val = stage[(size_t)c * cd.nvel + a] - rv;
+        val = stage[(size_t)c * cd.nvel + can] - rv;
     }
     T* dst = which == 0 ? cd.dh[cd.st->parity] : cd.db[cd.st->parity];
     dst[sidx(cd.nc, cd.nt, vb, c, n, lane)] = T(val);
@@ -601,11 +632,13 @@ __global__ void k_get_level(CaseDev<T> cd, int n, int which, double* stage)
     size_t r = k >> 5;
     int c = r % cd.nc, vb = r / cd.nc;
     int a = vb * VB + lane;
-    if (a >= cd.nvel) return;
+    const int can = cd.vcan[a];
+    // a node stored in several sign classes holds the same value in each; the first copy is read
+    if (can < 0 || cd.vcls[vb] != first_class(cd, can)) return;
     double href = (cd.lam0 / M_PI) * exp(-cd.lam0 * (cd.vu[a] * cd.vu[a] + cd.vv[a] * cd.vv[a]));
     double rv = which == 0 ? href : href * 0.5 / cd.lam0;
     const T* src = which == 0 ? cd.dh[cd.st->parity] : cd.db[cd.st->parity];
-    stage[(size_t)c * cd.nvel + a] = (double)src[sidx(cd.nc, cd.nt, vb, c, n, lane)] + rv;
+    stage[(size_t)c * cd.nvel + can] = (double)src[sidx(cd.nc, cd.nt, vb, c, n, lane)] + rv;
 }
 
 // uniform reduced Maxwellian (rho, U, V, T) on every level, delta form; W = its continuous moments
@@ -627,7 +660,7 @@ __global__ void k_init_uniform(CaseDev<T> cd, double rho, double U, double V, do
     int c = r % cd.nc, vb = r / cd.nc;
     int a = vb * VB + lane;
     double dhv = 0.0, dbv = 0.0;
-    if (a < cd.nvel) {
+    if (cd.vcan[a] >= 0) {
         double uu = cd.vu[a], vv = cd.vv[a];
         double lam = cd.lam0 / Tt;
         double H = rho * (lam / M_PI) * exp(-lam * ((uu - U) * (uu - U) + (vv - V) * (vv - V)));
