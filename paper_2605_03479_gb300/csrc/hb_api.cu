@@ -264,6 +264,7 @@ struct Impl {
     double* d_tol = nullptr;
     int* d_err = nullptr;
     int* d_off = nullptr;            // [table][ncases + 1]
+    int* d_tune_off = nullptr;       // block offsets of a single-case launch (autotuning)
     std::vector<int> off_host;
     std::vector<LaunchSpec> specs;   // in launch order (without the residual kernel)
     int k3_table = 0, steps_table = 0;
@@ -313,6 +314,7 @@ size_t plan(Impl<T>& im, int ncases, const hbugks_case* cases, char* base)
     im.d_status = cv.take<CaseStatus>(ncases);
     im.d_tol = cv.take<double>(1);
     im.d_err = cv.take<int>(1);
+    im.d_tune_off = cv.take<int>(2);
     // launch specs: K1 per shape, K2, K3, tables, K4 per shape; plus the step kernel (state setting only)
     im.specs.clear();
     auto add = [&](int kind, int shape) { im.specs.push_back(LaunchSpec{kind, shape, (int)im.specs.size(), 0, 0}); };
@@ -646,6 +648,109 @@ hbugks_status capture(hbugks_t h, Impl<T>& im)
     return HBUGKS_OK;
 }
 
+// every case at rest (rho 1, T0) on every level, fresh status, local steps of that state
+template <typename T>
+hbugks_status reset_rest(hbugks_t h, Impl<T>& im, int ncases)
+{
+    HB_CK(cudaMemsetAsync(im.d_tol, 0, sizeof(double), h->s));
+    HB_CK(cudaMemsetAsync(im.d_err, 0, sizeof(int), h->s));
+    k_status_reset<<<(ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, ncases, -1, 1);
+    for (int k = 0; k < ncases; ++k) {
+        const CaseDev<T>& d = im.dc[k];
+        size_t tot = (size_t)d.nc * d.nvb * VB * d.nt;
+        k_init_uniform<T><<<(unsigned)((tot + 255) / 256), 256, 0, h->s>>>(d, 1.0, 0.0, 0.0, 1.0);
+    }
+    enqueue_steps(im, ncases, h->s);
+    return HBUGKS_OK;
+}
+
+template <typename T>
+hbugks_status upload_offsets(hbugks_t h, Impl<T>& im)
+{
+    fill_offsets(im, h->ncases);
+    HB_CK(cudaMemcpyAsync(im.d_off, im.off_host.data(), sizeof(int) * im.off_host.size(), cudaMemcpyHostToDevice, h->s));
+    return HBUGKS_OK;
+}
+
+// ------------------------------------------------------------------------------ autotuner of the K4 tile
+// The micro update's tile (cells per CTA) trades halo re-reads and pass-1 work against shared memory per CTA
+// and so against CTAs per SM; which wins depends on the level count, the velocity grid, the mesh and the GPU.
+// Each feasible shape is timed on the case itself (one warm-up launch, then three), after one iteration from
+// rest has filled the parameters the kernel reads.  Choices are cached per process by everything that sets
+// the launch: mesh size, velocity grid, blocks, levels, precision and SM count.
+
+struct TuneCache {
+    std::mutex mu;
+    std::map<std::vector<int>, int> best;
+};
+TuneCache& tune_cache()
+{
+    static TuneCache c;
+    return c;
+}
+
+template <typename T>
+hbugks_status autotune(hbugks_t h, Impl<T>& im, int ncases)
+{
+    int dev = 0, sms = 0;
+    HB_CK(cudaGetDevice(&dev));
+    HB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    std::vector<std::vector<int>> keys(ncases);
+    bool need = false;
+    {
+        std::lock_guard<std::mutex> lk(tune_cache().mu);
+        for (int k = 0; k < ncases; ++k) {
+            const HostCase& hc = im.hc[k];
+            keys[k] = {hc.nx, hc.ny, hc.nu, hc.nv, hc.nvb, hc.nt, (int)sizeof(T), sms};
+            auto it = tune_cache().best.find(keys[k]);
+            if (it != tune_cache().best.end()) im.hc[k].k4shape = it->second;
+            else need = true;
+        }
+    }
+    if (need) {
+        k_begin_call<<<(ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, ncases);
+        enqueue_iteration(im, ncases, h->s);
+        k_begin_call<<<(ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, ncases);
+        cudaEvent_t e0, e1;
+        HB_CK(cudaEventCreate(&e0));
+        HB_CK(cudaEventCreate(&e1));
+        for (int k = 0; k < ncases; ++k) {
+            {
+                std::lock_guard<std::mutex> lk(tune_cache().mu);
+                auto it = tune_cache().best.find(keys[k]);
+                if (it != tune_cache().best.end()) { im.hc[k].k4shape = it->second; continue; }
+            }
+            HostCase& hc = im.hc[k];
+            int best = -1;
+            float best_ms = 0.f;
+            for (int sh = 0; sh < N_K4_SHAPES; ++sh) {
+                const size_t smem = k4_smem_of<T>(sh, hc.nt);
+                if (smem > SMEM_MAX) continue;
+                const Shape S = K4_SHAPES[sh];
+                const int off[2] = {0, ((hc.nx + S.tx - 1) / S.tx) * ((hc.ny + S.ty - 1) / S.ty) * hc.nvb};
+                HB_CK(cudaMemcpyAsync(im.d_tune_off, off, sizeof off, cudaMemcpyHostToDevice, h->s));
+                const Batch<T> b{im.d_cases + k, 1, im.d_tune_off};
+                launch_k4<T>(sh, off[1], smem, b, h->s);
+                HB_CK(cudaEventRecord(e0, h->s));
+                for (int r = 0; r < 3; ++r) launch_k4<T>(sh, off[1], smem, b, h->s);
+                HB_CK(cudaEventRecord(e1, h->s));
+                HB_CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                HB_CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (best < 0 || ms < best_ms) { best = sh; best_ms = ms; }
+            }
+            hc.k4shape = best;
+            std::lock_guard<std::mutex> lk(tune_cache().mu);
+            tune_cache().best[keys[k]] = best;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        HB_CK(cudaGetLastError());
+    }
+    for (auto& hc : im.hc) set_k4_blocks(hc);
+    return upload_offsets(h, im);
+}
+
 template <typename T>
 hbugks_status do_create(hbugks_t h, Impl<T>& im, int ncases, const hbugks_case* cases)
 {
@@ -657,15 +762,10 @@ hbugks_status do_create(hbugks_t h, Impl<T>& im, int ncases, const hbugks_case* 
     for (int k = 0; k < ncases; ++k) HB_CK(upload_case(im.hc[k], im.dc[k], h->s, keep));
     HB_CK(cudaMemcpyAsync(im.d_cases, im.dc.data(), sizeof(CaseDev<T>) * ncases, cudaMemcpyHostToDevice, h->s));
     HB_CK(cudaMemcpyAsync(im.d_off, im.off_host.data(), sizeof(int) * im.off_host.size(), cudaMemcpyHostToDevice, h->s));
-    HB_CK(cudaMemsetAsync(im.d_tol, 0, sizeof(double), h->s));
-    HB_CK(cudaMemsetAsync(im.d_err, 0, sizeof(int), h->s));
-    k_status_reset<<<(ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, ncases, -1, 1);
-    for (int k = 0; k < ncases; ++k) {
-        const CaseDev<T>& d = im.dc[k];
-        size_t tot = (size_t)d.nc * d.nvb * VB * d.nt;
-        k_init_uniform<T><<<(unsigned)((tot + 255) / 256), 256, 0, h->s>>>(d, 1.0, 0.0, 0.0, 1.0);
-    }
-    enqueue_steps(im, ncases, h->s);
+    hbugks_status rc = reset_rest(h, im, ncases);
+    if (rc == HBUGKS_OK) rc = autotune(h, im, ncases);
+    if (rc == HBUGKS_OK) rc = reset_rest(h, im, ncases);
+    if (rc != HBUGKS_OK) return rc;
     HB_CK(cudaStreamSynchronize(h->s));
     HB_CK(cudaGetLastError());
     return capture(h, im);
@@ -1102,6 +1202,39 @@ hbugks_status hbugks_harmonic_noalloc(int nx, int ny, int nu, int nv, const doub
     k_dft<<<(int)((8 * nc + 127) / 128), 128, 0, s>>>(scratch, nt, (int)nc, k, re, im);
     HB_CK(cudaGetLastError());
     return HBUGKS_OK;
+}
+
+hbugks_status hbugks_get_tile_shape(hbugks_t h, int case_index, int* tx, int* ty)
+{
+    if (!h || case_index < 0 || case_index >= h->ncases || !tx || !ty) return HBUGKS_EINVAL;
+    const int sh = dispatch(h, [&](auto& im) { return im.hc[case_index].k4shape; });
+    *tx = K4_SHAPES[sh].tx;
+    *ty = K4_SHAPES[sh].ty;
+    return HBUGKS_OK;
+}
+
+hbugks_status hbugks_set_tile_shape(hbugks_t h, int case_index, int tx, int ty)
+{
+    if (!h || case_index < 0 || case_index >= h->ncases) return HBUGKS_EINVAL;
+    int sh = -1;
+    for (int k = 0; k < N_K4_SHAPES; ++k)
+        if (K4_SHAPES[k].tx == tx && K4_SHAPES[k].ty == ty) sh = k;
+    if (sh < 0) return HBUGKS_EINVAL;
+    return dispatch(h, [&](auto& im) -> hbugks_status {
+        using T = typename std::remove_reference<decltype(*im.d_cases)>::type::value_type;
+        HostCase& hc = im.hc[case_index];
+        if (k4_smem_of<T>(sh, hc.nt) > SMEM_MAX) return HBUGKS_EINVAL;
+        hbugks_status rc = begin(h);
+        if (rc) return rc;
+        hc.k4shape = sh;
+        set_k4_blocks(hc);
+        if ((rc = upload_offsets(h, im)) != HBUGKS_OK) return rc;
+        HB_CK(cudaStreamSynchronize(h->s));
+        if (h->g1) { cudaGraphExecDestroy(h->g1); h->g1 = nullptr; }
+        if (h->gN) { cudaGraphExecDestroy(h->gN); h->gN = nullptr; }
+        if ((rc = capture(h, im)) != HBUGKS_OK) return rc;
+        return end(h);
+    });
 }
 
 int hbugks_launches_per_iteration(hbugks_t h)

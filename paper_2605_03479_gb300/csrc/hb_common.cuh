@@ -53,6 +53,7 @@ struct CaseStatus {
 
 template <typename T>
 struct CaseDev {
+    using value_type = T;
     int nx, ny, nu, nv, nvel, nvb, nt, nh, nfx, nf, nc;
     int face_step;
     double omega, mu0, w_vss, pr, cfl, gam, umax, vmax, lam0;

@@ -58,7 +58,8 @@ EXPORTED = ("hbugks_workspace_bytes", "hbugks_create", "hbugks_destroy", "hbugks
             "hbugks_set_state", "hbugks_get_state", "hbugks_iterate", "hbugks_set_active",
             "hbugks_residual_history", "hbugks_get_level_fields", "hbugks_get_harmonic", "hbugks_iteration_count",
             "hbugks_status_string", "hbugks_enqueue_iterations", "hbugks_profile_kernels",
-            "hbugks_harmonic_noalloc", "hbugks_launches_per_iteration")
+            "hbugks_harmonic_noalloc", "hbugks_launches_per_iteration", "hbugks_get_tile_shape",
+            "hbugks_set_tile_shape")
 
 
 def lib():
@@ -94,6 +95,8 @@ def lib():
             L.hbugks_profile_kernels.argtypes = [vp, i, pd]
             L.hbugks_harmonic_noalloc.argtypes = [i, i, i, i, vp, vp, vp, vp, i, vp, vp, i, vp, vp, vp]
             L.hbugks_launches_per_iteration.argtypes = [vp]
+            L.hbugks_get_tile_shape.argtypes = [vp, i, C.POINTER(i), C.POINTER(i)]
+            L.hbugks_set_tile_shape.argtypes = [vp, i, i, i]
             for name in EXPORTED:
                 if name not in ("hbugks_workspace_bytes", "hbugks_destroy", "hbugks_iteration_count",
                                 "hbugks_status_string"):
@@ -245,6 +248,16 @@ class Solver:
 
     def launches_per_iteration(self) -> int:
         return int(lib().hbugks_launches_per_iteration(self.h))
+
+    def tile_shape(self, case_index: int = 0) -> tuple[int, int]:
+        """Micro-update tile (cells along x, y per CTA) chosen for a case by the autotuner or pinned."""
+        tx, ty = C.c_int(0), C.c_int(0)
+        _check(lib().hbugks_get_tile_shape(self.h, case_index, C.byref(tx), C.byref(ty)), "get_tile_shape")
+        return tx.value, ty.value
+
+    def set_tile_shape(self, case_index: int, tx: int, ty: int) -> None:
+        """Pin the micro-update tile of a case (4x4, 4x2 or 2x2)."""
+        _check(lib().hbugks_set_tile_shape(self.h, case_index, tx, ty), "set_tile_shape")
 
     # ------------------------------------------------------------------ fields
     def level_fields(self, case_index: int, level: int):
