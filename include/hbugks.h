@@ -189,7 +189,7 @@ HBUGKS_API hbugks_status hbugks_harmonic_noalloc(int nx, int ny, int nu, int nv,
 /* Tile of the micro-update kernel (cells along x and y handled by one CTA, all levels of one block of 32
  * velocities).  hbugks_create() picks it per case by timing every tile that fits in shared memory on the case
  * itself (autotuning, cached per process by mesh size, velocity grid, level count, precision and SM count).
- * get: the tile of case `case_index`.  set: pin a tile (4x4, 4x2 or 2x2), for example to reproduce a run
+ * get: the tile of case `case_index`.  set: pin a tile (4x4, 4x2, 2x2 or 8x4), for example to reproduce a run
  * exactly; HBUGKS_EINVAL if the tile is not one of these or needs more shared memory than a CTA may have.
  * The state is unchanged; the iteration graphs are rebuilt.  The paper has no counterpart (a GPU tuning
  * choice). */

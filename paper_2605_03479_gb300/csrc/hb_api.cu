@@ -80,8 +80,8 @@ constexpr size_t k1_smem_of()
 struct Shape {
     int tx, ty, nw;
 };
-constexpr Shape K4_SHAPES[] = {{4, 4, 8}, {4, 2, 8}, {2, 2, 4}};
-constexpr int N_K4_SHAPES = 3;
+constexpr Shape K4_SHAPES[] = {{4, 4, 8}, {4, 2, 8}, {2, 2, 4}, {8, 4, 16}};
+constexpr int N_K4_SHAPES = 4;
 
 template <typename T>
 size_t k4_smem_of(int shape, int nt)
@@ -89,7 +89,8 @@ size_t k4_smem_of(int shape, int nt)
     switch (shape) {
         case 0: return k4_cells_smem<T, 4, 4>(nt);
         case 1: return k4_cells_smem<T, 4, 2>(nt);
-        default: return k4_cells_smem<T, 2, 2>(nt);
+        case 2: return k4_cells_smem<T, 2, 2>(nt);
+        default: return k4_cells_smem<T, 8, 4>(nt);
     }
 }
 
@@ -557,7 +558,8 @@ void launch_k4(int shape, int total, size_t smem, Batch<T> b, cudaStream_t s)
     switch (shape) {
         case 0: k4_cells<T, 4, 4, 8><<<total, 8 * 32, smem, s>>>(b); break;
         case 1: k4_cells<T, 4, 2, 8><<<total, 8 * 32, smem, s>>>(b); break;
-        default: k4_cells<T, 2, 2, 4><<<total, 4 * 32, smem, s>>>(b); break;
+        case 2: k4_cells<T, 2, 2, 4><<<total, 4 * 32, smem, s>>>(b); break;
+        default: k4_cells<T, 8, 4, 16><<<total, 16 * 32, smem, s>>>(b); break;
     }
 }
 
@@ -571,6 +573,7 @@ cudaError_t set_smem_attributes()
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k4_cells<T, 4, 4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k4_cells<T, 4, 2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k4_cells<T, 2, 2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k4_cells<T, 8, 4, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     return e;
 }
 

@@ -277,25 +277,21 @@ constexpr size_t k1_cells_smem()
 // ------------------------------------------------------------------------------ K4: micro update
 
 // Micro flux (delta form, divided by dG_f) through the downwind face of the reconstructing cell, for one lane:
-// u_n [C1' dH + H Q + C4' d0 + C5' (u_n s_n + u_t s_t)] and the b counterpart, with the face's parameters fp
-// (cubic and linear terms of the upwind side `neg`: the high-side cell for u_n < 0) and expm1 factors tb.
+// u_n [C1' dH + H Q + C4' d0 + C5' (u_n s_n + u_t s_t)] and the b counterpart, from the face's parameters fp
+// (shared memory; the cubic at qo and linear term at lo belong to the upwind side) and the expm1 factors
+// (ex, ey) of the interface Maxwellian at the lane's velocity.
 template <typename T>
-__device__ __forceinline__ void flux_down(const T* __restrict__ fp, const T* __restrict__ tb, int iu, int ivn, T href,
-                                          T u, T v, T un, T ut, bool neg, T d0, T e0, T sn, T st, T snb, T stb, T& Hf,
-                                          T& Bf)
+__device__ __forceinline__ void flux_down(const T* fp, int qo, int lo, T ex, T ey, T href, T u, T v, T un, T ut, T d0,
+                                          T e0, T sn, T st, T snb, T stb, T& Hf, T& Bf)
 {
-    T sc[8];
-    ldv<8>(fp + F_RM1, sc);        // r - 1, r, 1/(2 lam), 1/(2 lam) - 1/(2 lam0), C1', C4', C5', nin
-    const T ex = __ldg(tb + iu), ey = __ldg(tb + ivn);
+    const T* sc = fp + F_RM1;      // r - 1, r, 1/(2 lam), 1/(2 lam) - 1/(2 lam0), C1', C4', C5', nin
     const T E = ex + ey + ex * ey;
     const T dH = href * (sc[0] + sc[1] * E);
     const T H = href + dH;
     const T i2l = sc[2];
     const T dB = dH * i2l + href * sc[3];
-    T q[12], l[4];
-    ldv<12>(fp + (neg ? F_QR : F_QL), q);
-    ldv<4>(fp + (neg ? F_LBR : F_LBL), l);
-    const T Q = cubic(q, u, v);
+    const T* l = fp + lo;
+    const T Q = cubic(fp + qo, u, v);
     const T Qb = Q + l[0] + l[1] * u + l[2] * v;
     Hf = un * (sc[4] * dH + H * Q + sc[5] * d0 + sc[6] * (un * sn + ut * st));
     Bf = un * (sc[4] * dB + H * i2l * Qb + sc[5] * e0 + sc[6] * (un * snb + ut * stb));
@@ -305,11 +301,10 @@ __device__ __forceinline__ void flux_down(const T* __restrict__ fp, const T* __r
 // Flux (delta form, divided by dG_f) of the distribution a diffuse wall re-emits, rho_w H_w u_n: velocities of
 // the block leave the wall.
 template <typename T>
-__device__ __forceinline__ void flux_wall(const T* __restrict__ fp, const T* __restrict__ tb, int iu, int ivn, T href,
-                                          T un, T& Hf, T& Bf)
+__device__ __forceinline__ void flux_wall(const T* fp, const T* __restrict__ tb, int iu, int ivn, T href, T un, T& Hf,
+                                          T& Bf)
 {
-    T wp[4];
-    ldv<4>(fp + F_WRM1, wp);
+    const T* wp = fp + F_WRM1;
     const T ex = __ldg(tb + iu), ey = __ldg(tb + ivn);
     const T E = ex + ey + ex * ey;
     const T dHw = href * (wp[0] + wp[1] * E);
@@ -317,64 +312,135 @@ __device__ __forceinline__ void flux_wall(const T* __restrict__ fp, const T* __r
     Bf = un * (dHw * wp[2] + href * wp[3]);
 }
 
-// A CTA: a TX x TY tile of cells, one velocity block, all levels.  The staged rectangle holds the tile, two
-// cells of halo on the upwind side of each axis and one on the downwind side.  Per level, the first pass
-// reconstructs every tile cell and the upwind halo cells and evaluates the flux through each one's downwind
-// face (every face of the tile exactly once); the second pass applies Eq. fv_h to the tile cells.  The
-// second pass of level n runs together with the first pass of level n + 1 (the face fluxes are double
-// buffered), so one barrier separates the levels.
+// Shared-memory layout of k4_cells (element offsets in T, each block 16-byte aligned):
+//   own   [nt][h, b][NCT][32]      the tile's own cells on every level (spectral source, h^k of the update)
+//   rect  [2][h, b][NR][32]        per level: the tile with its halo, (TX+3) x (TY+3) cells, two cells on the
+//                                  upwind side of each axis and one on the downwind side (ring of 2 levels)
+//   fp    [2][NFT][NP]             per level: parameters of the tile's faces (ring of 2 levels)
+//   cp    [2][NCT][NCP]            per level: update coefficients of the tile's cells (ring of 2 levels)
+//   flux  [2][h, b][NFT][32]       per level: micro fluxes of the tile's faces (double buffered)
+template <typename T, int TX, int TY>
+struct K4Layout {
+    static constexpr int PX = TX + 3, PY = TY + 3, NR = PX * PY, NCT = TX * TY;
+    static constexpr int NFX = TY * (TX + 1), NFY = (TY + 1) * TX, NFT = NFX + NFY;
+    static constexpr size_t RECT = (size_t)2 * NR * VB;                 // one ring slot, h and b
+    static constexpr size_t FP = (size_t)NFT * NP, CP = (size_t)NCT * NCP, FLUX = (size_t)2 * NFT * VB;
+    __host__ __device__ static constexpr size_t own_elems(int nt) { return (size_t)nt * 2 * NCT * VB; }
+    __host__ __device__ static constexpr size_t rect_off(int nt) { return own_elems(nt); }
+    __host__ __device__ static constexpr size_t fp_off(int nt) { return rect_off(nt) + 2 * RECT; }
+    __host__ __device__ static constexpr size_t cp_off(int nt) { return fp_off(nt) + 2 * FP; }
+    __host__ __device__ static constexpr size_t flux_off(int nt) { return cp_off(nt) + 2 * CP; }
+    __host__ __device__ static constexpr size_t bytes(int nt) { return (flux_off(nt) + 2 * FLUX) * sizeof(T); }
+};
+
+// A CTA: a TX x TY tile of cells, one velocity block, all levels.  Per level, the first pass reconstructs
+// every tile cell and the upwind halo cells and evaluates the flux through each one's downwind face (every
+// face of the tile exactly once); the second pass applies Eq. fv_h to the tile cells.  The second pass of
+// level n runs together with the first pass of level n + 1 (fluxes double buffered), so one barrier separates
+// the levels.  Batch k of bulk copies (the halo rectangle and face parameters of level k, the cell
+// coefficients of level k - 1; batch 0 also every level of the tile's own cells) completes on mbarrier k & 1
+// and is issued one level ahead of its use.
 template <typename T, int TX, int TY, int NW>
 __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
 {
-    constexpr int PX = TX + 3, PY = TY + 3, NR = PX * PY;
-    constexpr int NCT = TX * TY, NFX = TY * (TX + 1), NFY = (TY + 1) * TX, NFT = NFX + NFY;
+    using L = K4Layout<T, TX, TY>;
+    constexpr int PX = L::PX, PY = L::PY, NR = L::NR, NCT = L::NCT, NFX = L::NFX, NFT = L::NFT;
     constexpr int NIT = NCT + TY + TX, NPASS = (NIT + NW - 1) / NW;
-    constexpr int lv = NR * VB;                               // one staged level of one array
+    constexpr int lv = NR * VB;                               // one array of one rectangle slot
+    constexpr int SROWS = 4;                                  // tile rows per strip of the CTA order
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ uint64_t bar[1];
+    __shared__ uint64_t bars[2];
     __shared__ T gxr[PX], gxh[PX], gyr[PY], gyh[PY];
     const int cs = find_case(B.off, B.ncases, blockIdx.x);
     const CaseDev<T>& cd = B.cases[cs];
     if (!cd.st->active) return;
-    const int nvb = cd.nvb;
-    // velocity block fastest: the CTAs of one tile run together and share its face and cell parameters in L2
+    const int nvb = cd.nvb, nx = cd.nx, ny = cd.ny;
+    // CTA order: velocity block fastest (the CTAs of one tile share its parameters in L2), then tiles in
+    // strips of SROWS tile rows, column by column (neighbour tiles, whose halos overlap, run close in time)
     const int lb = blockIdx.x - B.off[cs];
     const int vb = lb % nvb, tile = lb / nvb;
-    const int ntx = (cd.nx + TX - 1) / TX;
-    const int i0 = (tile % ntx) * TX, j0 = (tile / ntx) * TY;
-    const int nt = cd.nt, nc = cd.nc, nx = cd.nx, ny = cd.ny, nh = cd.nh, nfx = cd.nfx;
+    const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY;
+    const int strip = tile / (ntx * SROWS), rows = min(SROWS, nty - strip * SROWS);
+    const int rem = tile - strip * ntx * SROWS;
+    const int i0 = (rem / rows) * TX, j0 = (strip * SROWS + rem % rows) * TY;
+    const int nt = cd.nt, nc = cd.nc, nh = cd.nh, nfx = cd.nfx, nf = cd.nf;
     const int nuv = cd.nu + cd.nv;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cls = __ldg(cd.vcls + vb);
     const bool xneg = (cls & 1) != 0, yneg = (cls & 2) != 0;
     const int xlo = xneg ? -1 : -2, ylo = yneg ? -1 : -2;
     const int iend = min(i0 + TX, nx), jend = min(j0 + TY, ny);
-    T* sh = reinterpret_cast<T*>(smem_raw);
-    T* sb = sh + nt * lv;
-    T* fbuf = sb + nt * lv;    // [level parity][h, b][NFT][32]
-    mbar_setup(bar, 1);
+    T* const sm = reinterpret_cast<T*>(smem_raw);
+    T* const own = sm;
+    T* const rect = sm + L::rect_off(nt);
+    T* const fps = sm + L::fp_off(nt);
+    T* const cps = sm + L::cp_off(nt);
+    T* const fbuf = sm + L::flux_off(nt);
+    mbar_setup(bars, 2);
     const int p = cd.st->parity;
+    const T* gh = cd.dh[p];
+    const T* gb = cd.db[p];
+    // bulk copies of the rectangle rows (clipped to the domain)
     const int c0 = max(i0 + xlo, 0), c1 = min(i0 + xlo + PX, nx);
-    if (warp == 0) {
-        uint32_t rb = 0;
-        for (int r = 0; r < PY; ++r) {
-            const int jj = j0 + ylo + r;
-            if (jj >= 0 && jj < ny && c1 > c0) rb += (uint32_t)((c1 - c0) * VB * sizeof(T));
-        }
-        if (lane == 0) mbar_arrive_expect(bar, (uint32_t)(2 * nt) * rb);
-        __syncwarp();
-        const T* gh = cd.dh[p];
-        const T* gb = cd.db[p];
-        for (int q = lane; q < 2 * nt * PY; q += 32) {
-            const int r = q % PY, na = q / PY;   // na = 2 n + array
-            const int jj = j0 + ylo + r;
-            if (jj < 0 || jj >= ny || c1 <= c0) continue;
-            const int n = na >> 1;
-            const size_t src = ((size_t)vb * nt + n) * nc * VB + ((size_t)jj * nx + c0) * VB;
-            bulk_g2s(((na & 1) ? sb : sh) + n * lv + (r * PX + c0 - (i0 + xlo)) * VB, ((na & 1) ? gb : gh) + src,
-                     (uint32_t)((c1 - c0) * VB * sizeof(T)), bar);
-        }
+    const int nfr = iend - i0;                                // valid cells per tile row
+    const uint32_t row_b = (uint32_t)((c1 - c0) * VB * sizeof(T));
+    int rrows = 0;
+    for (int r = 0; r < PY; ++r) {
+        const int jj = j0 + ylo + r;
+        rrows += (jj >= 0 && jj < ny) ? 1 : 0;
     }
+    const uint32_t rect_b = 2u * rrows * row_b;
+    const uint32_t fp_b = (uint32_t)(((jend - j0) * (nfr + 1) + (jend - j0 + 1) * nfr) * NP * sizeof(T));
+    const uint32_t cp_b = (uint32_t)((jend - j0) * nfr * NCP * sizeof(T));
+    // batch k: rectangle and face parameters of level k (k < nt), cell coefficients of level k - 1 (k >= 1)
+    auto issue = [&](int k) {
+        const bool lvl = k < nt, cel = k >= 1;
+        uint32_t bytes = (lvl ? rect_b + fp_b : 0u) + (cel ? cp_b : 0u);
+        if (k == 0) bytes += (uint32_t)(2 * nt * (jend - j0) * nfr * VB * sizeof(T));
+        uint64_t* bar = &bars[k & 1];
+        if (lane == 0) mbar_arrive_expect(bar, bytes);
+        __syncwarp();
+        const int nrect = lvl ? 2 * PY : 0, nfpr = lvl ? 2 * TY + 1 : 0, ncpr = cel ? TY : 0;
+        const int nown = k == 0 ? 2 * nt * TY : 0;
+        for (int q = lane; q < nrect + nfpr + ncpr + nown; q += 32) {
+            if (q < nrect) {
+                const int r = q % PY, a = q / PY;
+                const int jj = j0 + ylo + r;
+                if (jj < 0 || jj >= ny) continue;
+                const size_t src = ((size_t)vb * nt + k) * nc * VB + ((size_t)jj * nx + c0) * VB;
+                bulk_g2s(rect + (size_t)(k & 1) * L::RECT + (size_t)a * lv + (r * PX + c0 - (i0 + xlo)) * VB,
+                         (a ? gb : gh) + src, row_b, bar);
+            } else if (q < nrect + nfpr) {
+                const int r = q - nrect;
+                if (r < TY) {                                 // x-faces of tile row r
+                    const int jj = j0 + r;
+                    if (jj >= ny) continue;
+                    bulk_g2s(fps + (size_t)(k & 1) * L::FP + (size_t)r * (TX + 1) * NP,
+                             cd.fpar + ((size_t)k * nf + jj * (nx + 1) + i0) * NP,
+                             (uint32_t)((nfr + 1) * NP * sizeof(T)), bar);
+                } else {                                      // y-faces of face row r - TY
+                    const int fr = r - TY, jj = j0 + fr;
+                    if (jj > jend) continue;
+                    bulk_g2s(fps + (size_t)(k & 1) * L::FP + (size_t)(NFX + fr * TX) * NP,
+                             cd.fpar + ((size_t)k * nf + nfx + jj * nx + i0) * NP, (uint32_t)(nfr * NP * sizeof(T)),
+                             bar);
+                }
+            } else if (q < nrect + nfpr + ncpr) {
+                const int r = q - nrect - nfpr, jj = j0 + r;  // cells of tile row r, level k - 1
+                if (jj >= ny) continue;
+                bulk_g2s(cps + (size_t)((k - 1) & 1) * L::CP + (size_t)r * TX * NCP,
+                         cd.cpar + ((size_t)(k - 1) * nc + jj * nx + i0) * NCP, (uint32_t)(nfr * NCP * sizeof(T)), bar);
+            } else {
+                const int o = q - nrect - nfpr - ncpr;        // own cells: row, array, level
+                const int r = o % TY, a = (o / TY) & 1, n = o / (2 * TY), jj = j0 + r;
+                if (jj >= ny) continue;
+                bulk_g2s(own + ((size_t)(n * 2 + a) * NCT + r * TX) * VB,
+                         (a ? gb : gh) + ((size_t)vb * nt + n) * nc * VB + ((size_t)jj * nx + i0) * VB,
+                         (uint32_t)(nfr * VB * sizeof(T)), bar);
+            }
+        }
+    };
+    if (warp == 0) issue(0);
     for (int k = threadIdx.x; k < PX; k += blockDim.x) {
         const int ii = i0 + xlo + k;
         gxr[k] = (ii >= 0 && ii < nx - 1) ? T(cd.rdx[ii]) : T(0);
@@ -391,23 +457,26 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
     T et[8];
 #pragma unroll
     for (int d = 0; d < 8; ++d) et[d] = cd.et[d];
-    const T* __restrict__ fpar = cd.fpar;
     const T* __restrict__ ftab = cd.ftab;
     const T* __restrict__ wtab = cd.wtab;
-    const T* __restrict__ cpar = cd.cpar;
     const T* __restrict__ ctab = cd.ctab;
     const bool shakhov = cd.shakhov != 0;
-    const int NPf = nt * NP, NTf = nt * nuv;            // per-face strides of the face parameters and tables
-    const int fail = !mbar_wait(bar, 0u, cd.err);
-    if (__syncthreads_or(fail)) return;
+    const int NTf = nt * nuv;                                 // per-face stride of the expm1 tables
+    const int qoff = xneg ? F_QR : F_QL, loff = xneg ? F_LBR : F_LBL;
+    const int qoffy = yneg ? F_QR : F_QL, loffy = yneg ? F_LBR : F_LBL;
+    int* err = cd.err;
 
     for (int s = 0; s <= nt; ++s) {
+        if (warp == 0 && s < nt) issue(s + 1);
+        const int fail = !mbar_wait(&bars[s & 1], (uint32_t)((s >> 1) & 1), err);
+        if (__syncthreads_or(fail)) return;
         if (s < nt) {
             // ---- pass 1, level s: reconstruction and downwind-face fluxes
             const int n = s;
-            T* Fh = fbuf + (n & 1) * 2 * NFT * VB + lane;
+            T* Fh = fbuf + (size_t)(n & 1) * L::FLUX + lane;
             T* Fb = Fh + NFT * VB;
-            const T* fpn = fpar + n * NP;
+            const T* rh = rect + (size_t)(n & 1) * L::RECT + lane;
+            const T* fpn = fps + (size_t)(n & 1) * L::FP;
             const T* ftn = ftab + n * nuv;
 #pragma unroll
             for (int r = 0; r < NPASS; ++r) {
@@ -431,21 +500,29 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
                     T Hf, Bf;
                     int slot;
                     if (dox) {
-                        const int fi = i < 0 ? 0 : nx, gface = j * (nx + 1) + fi;
-                        flux_wall(fpn + gface * NPf, wtab + ((i < 0 ? 3 : 1) * nt + n) * nuv, iu, ivn, href, u, Hf, Bf);
+                        const int fi = i < 0 ? 0 : nx;
                         slot = tj * (TX + 1) + fi - i0;
+                        flux_wall(fpn + slot * NP, wtab + ((i < 0 ? 3 : 1) * nt + n) * nuv, iu, ivn, href, u, Hf, Bf);
                     } else {
-                        const int fj = j < 0 ? 0 : ny, gface = nfx + fj * nx + i;
-                        flux_wall(fpn + gface * NPf, wtab + ((j < 0 ? 0 : 2) * nt + n) * nuv, iu, ivn, href, v, Hf, Bf);
+                        const int fj = j < 0 ? 0 : ny;
                         slot = NFX + (fj - j0) * TX + ti;
+                        flux_wall(fpn + slot * NP, wtab + ((j < 0 ? 0 : 2) * nt + n) * nuv, iu, ivn, href, v, Hf, Bf);
                     }
                     Fh[slot * VB] = Hf;
                     Fb[slot * VB] = Bf;
                     continue;
                 }
                 const int kx = ti - xlo, ky = tj - ylo;
-                const T* ph = sh + n * lv + (ky * PX + kx) * VB + lane;
-                const T* pb = ph + nt * lv;
+                const int fix = xneg ? i : i + 1, fjy = yneg ? j : j + 1;
+                const int slx = tj * (TX + 1) + fix - i0, sly = NFX + (fjy - j0) * TX + ti;
+                // expm1 factors of the interface Maxwellians first: their latency overlaps the reconstruction
+                const T* tbx = ftn + (j * (nx + 1) + fix) * NTf;
+                const T* tby = ftn + (nfx + fjy * nx + i) * NTf;
+                T exx = T(0), eyx = T(0), exy = T(0), eyy = T(0);
+                if (dox) { exx = __ldg(tbx + iu); eyx = __ldg(tbx + ivn); }
+                if (doy) { exy = __ldg(tby + iu); eyy = __ldg(tby + ivn); }
+                const T* ph = rh + (ky * PX + kx) * VB;
+                const T* pb = ph + lv;
                 const T f0 = ph[0], g0 = pb[0];
                 const bool hm = i > 0, hp = i < nx - 1, vm = j > 0, vp = j < ny - 1;
                 const T wxm = gxr[kx - 1], wxp = gxr[kx], wym = gyr[ky - 1], wyp = gyr[ky];
@@ -454,36 +531,33 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
                 const T syh = slope(ph[-PX * VB], f0, ph[PX * VB], wym, wyp, vm, vp, ny > 1);
                 const T syb = slope(pb[-PX * VB], g0, pb[PX * VB], wym, wyp, vm, vp, ny > 1);
                 if (dox) {
-                    const int fi = xneg ? i : i + 1, gface = j * (nx + 1) + fi;
                     const T off = xneg ? -gxh[kx] : gxh[kx];
                     T Hf, Bf;
-                    flux_down(fpn + gface * NPf, ftn + gface * NTf, iu, ivn, href, u, v, u, v, xneg, f0 + sxh * off,
-                              g0 + sxb * off, sxh, syh, sxb, syb, Hf, Bf);
-                    const int slot = tj * (TX + 1) + fi - i0;
-                    Fh[slot * VB] = Hf;
-                    Fb[slot * VB] = Bf;
+                    flux_down(fpn + slx * NP, qoff, loff, exx, eyx, href, u, v, u, v, f0 + sxh * off, g0 + sxb * off,
+                              sxh, syh, sxb, syb, Hf, Bf);
+                    Fh[slx * VB] = Hf;
+                    Fb[slx * VB] = Bf;
                 }
                 if (doy) {
-                    const int fj = yneg ? j : j + 1, gface = nfx + fj * nx + i;
                     const T off = yneg ? -gyh[ky] : gyh[ky];
                     T Hf, Bf;
-                    flux_down(fpn + gface * NPf, ftn + gface * NTf, iu, ivn, href, u, v, v, u, yneg, f0 + syh * off,
-                              g0 + syb * off, syh, sxh, syb, sxb, Hf, Bf);
-                    const int slot = NFX + (fj - j0) * TX + ti;
-                    Fh[slot * VB] = Hf;
-                    Fb[slot * VB] = Bf;
+                    flux_down(fpn + sly * NP, qoffy, loffy, exy, eyy, href, u, v, v, u, f0 + syh * off, g0 + syb * off,
+                              syh, sxh, syb, sxb, Hf, Bf);
+                    Fh[sly * VB] = Hf;
+                    Fb[sly * VB] = Bf;
                 }
             }
         }
         if (s > 0) {
             // ---- pass 2, level s - 1: Eq. fv_h with the spectral source (delta form)
             const int n = s - 1;
-            const T* Fh = fbuf + (n & 1) * 2 * NFT * VB + lane;
+            const T* Fh = fbuf + (size_t)(n & 1) * L::FLUX + lane;
             const T* Fb = Fh + NFT * VB;
             T* on = cd.dh[p ^ 1] + ((size_t)vb * nt + n) * nc * VB + lane;
             T* onb = cd.db[p ^ 1] + ((size_t)vb * nt + n) * nc * VB + lane;
-            const T* cpn = cpar + n * NCP;
+            const T* cpn = cps + (size_t)(n & 1) * L::CP;
             const T* ctn = ctab + n * 2 * nuv;
+            constexpr int lvo = 2 * NCT * VB;                 // level stride of the own-cell store
 #pragma unroll
             for (int r = 0; r < (NCT + NW - 1) / NW; ++r) {
                 const int ct = warp + r * NW;
@@ -492,34 +566,34 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
                 const int i = i0 + ti, j = j0 + tj;
                 if (i >= nx || j >= ny) continue;
                 const int c = j * nx + i;
+                const T* tb = ctn + c * nt * 2 * nuv;
+                const T ex0 = __ldg(tb + iu), ey0 = __ldg(tb + ivn);
+                const T ex1 = __ldg(tb + nuv + iu), ey1 = __ldg(tb + nuv + ivn);
                 const int fL = tj * (TX + 1) + ti, fB = NFX + tj * TX + ti;
                 const T dxh = Fh[(fL + 1) * VB] - Fh[fL * VB];
                 const T dyh = Fh[(fB + TX) * VB] - Fh[fB * VB];
                 const T dxb = Fb[(fL + 1) * VB] - Fb[fL * VB];
                 const T dyb = Fb[(fB + TX) * VB] - Fb[fB * VB];
-                const int kc = ((tj - ylo) * PX + ti - xlo) * VB + lane;
-                const T* hc = sh + kc;     // level m at hc[m * lv]
-                const T* bc = sb + kc;
+                const T* hc = own + ct * VB + lane;          // level m, array a at hc[m * lvo + a * NCT * VB]
+                const T* bc = hc + NCT * VB;
                 T eh, eb;
                 switch (nh) {
                     case 0: eh = T(0); eb = T(0); break;
-                    case 1: spectral<1>(hc, bc, n, nt, lv, et, eh, eb); break;
-                    case 2: spectral<2>(hc, bc, n, nt, lv, et, eh, eb); break;
-                    case 3: spectral<3>(hc, bc, n, nt, lv, et, eh, eb); break;
-                    case 4: spectral<4>(hc, bc, n, nt, lv, et, eh, eb); break;
-                    case 5: spectral<5>(hc, bc, n, nt, lv, et, eh, eb); break;
-                    case 6: spectral<6>(hc, bc, n, nt, lv, et, eh, eb); break;
-                    default: spectral<7>(hc, bc, n, nt, lv, et, eh, eb); break;
+                    case 1: spectral<1>(hc, bc, n, nt, lvo, et, eh, eb); break;
+                    case 2: spectral<2>(hc, bc, n, nt, lvo, et, eh, eb); break;
+                    case 3: spectral<3>(hc, bc, n, nt, lvo, et, eh, eb); break;
+                    case 4: spectral<4>(hc, bc, n, nt, lvo, et, eh, eb); break;
+                    case 5: spectral<5>(hc, bc, n, nt, lvo, et, eh, eb); break;
+                    case 6: spectral<6>(hc, bc, n, nt, lvo, et, eh, eb); break;
+                    default: spectral<7>(hc, bc, n, nt, lvo, et, eh, eb); break;
                 }
                 // equilibria of W^{k+1} (slot 1) and W^k (slot 0): dH = H - H_ref from the cell table, Shakhov cubic
-                const T* cp = cpn + c * nt * NCP;
-                const T* tb = ctn + c * nt * 2 * nuv;
+                const T* cp = cpn + ct * NCP;
                 T dhp[2], dbp[2];
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                    T q[20];
-                    ldv<20>(cp + (e == 0 ? C_EQ0 : C_EQ1), q);
-                    const T ex = __ldg(tb + e * nuv + iu), ey = __ldg(tb + e * nuv + ivn);
+                    const T* q = cp + (e == 0 ? C_EQ0 : C_EQ1);
+                    const T ex = e == 0 ? ex0 : ex1, ey = e == 0 ? ey0 : ey1;
                     const T E = ex + ey + ex * ey;
                     const T dH = href * (q[E_RM1] + q[E_R] * E);
                     const T dB = dH * q[E_I2L] + href * q[E_DI2L];
@@ -534,9 +608,8 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
                         dbp[e] = dB;
                     }
                 }
-                T k[8];
-                ldv<8>(cp + C_KSELF, k);           // kself, kE, kp1, kp0, kdx, kdy
-                const T h0 = hc[n * lv], b0 = bc[n * lv];
+                const T* k = cp + C_KSELF;                    // kself, kE, kp1, kp0, kdx, kdy
+                const T h0 = hc[n * lvo], b0 = bc[n * lvo];
                 on[c * VB] = k[0] * h0 - k[4] * dxh - k[5] * dyh - k[1] * eh + k[2] * dhp[1] + k[3] * dhp[0];
                 onb[c * VB] = k[0] * b0 - k[4] * dxb - k[5] * dyb - k[1] * eb + k[2] * dbp[1] + k[3] * dbp[0];
             }
@@ -548,8 +621,7 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
 template <typename T, int TX, int TY>
 constexpr size_t k4_cells_smem(int nt)
 {
-    return round16(((size_t)2 * nt * (TX + 3) * (TY + 3) * VB + (size_t)2 * 2 * (TY * (TX + 1) + (TY + 1) * TX) * VB) *
-                   sizeof(T));
+    return K4Layout<T, TX, TY>::bytes(nt);
 }
 
 }  // namespace hb

@@ -77,7 +77,7 @@ struct CaseDev {
     double* dG;
     double* hmom;                      // [nc][nt][4][NM] half-face sums of the reconstruction per sign class
     double* cmom;                      // [nc][nt][NCM]
-    T* fpar;                           // [nf][nt][NP]
+    T* fpar;                           // [nt][nf][NP]
     T* ftab;                           // [nf][nt][nu + nv]   expm1 factors of the interface Maxwellian
     T* wtab;                           // [4][nt][nu + nv]  expm1 factors of each wall's Maxwellian
     T* ctab;                           // [nc][nt][2][nu + nv] expm1 factors of the cell equilibria (W^k, W^{k+1})
@@ -87,7 +87,7 @@ struct CaseDev {
     const int* vcls;                   // per velocity block: sign class (bit 0: u < 0, bit 1: v < 0)
     int shakhov;                       // Pr != 1
     double* fflux;                     // [nf][nt][4]
-    T* cpar;                           // [nc][nt][NCP]
+    T* cpar;                           // [nt][nc][NCP]
     double* rpart;                     // [k3 blocks][4]
     double* rhist;                     // [RING][4]
     double* stage;                     // conversion staging (>= nc * nvel_pad doubles)

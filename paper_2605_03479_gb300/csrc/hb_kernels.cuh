@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
     // ---- parameters of the micro flux (delta form, divided by dG_f): for each upwind side the cubic
     // Q = C1' s(c.q)(2 lam |c|^2 - 4) + C2' (u_n P_h(a_side) + u_t P_h(a_t)) + C3' P_h(A) and the linear b-part
     // difference C1' 2 s (c.q) + C2' (u_n a_side,3 + u_t a_t,3)/(2 lam) + C3' A_3/(2 lam)
-    T* pp = cd.fpar + (size_t)item * NP;
+    T* pp = cd.fpar + ((size_t)n * cd.nf + f) * NP;      // level-major: a tile's faces of one level are rows
     const T C1p = T(C[0] / dGf), C2p = T(C[1] / dGf), C3p = T(C[2] / dGf);
     for (int side = 0; side < 2; ++side) {
         const PolyT<T>& Qs = side == 0 ? QL : QR;
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(K3_THREADS) k3_macro(Batch<T> B)
             heat_flux_raw(A, U0, V0, qx, qy);
             const double t0 = relax_time(cd.mu0, cd.w_vss, cd.lam0, r0, l0);
             const double t1 = relax_time(cd.mu0, cd.w_vss, cd.lam0, r1, l1);
-            T* cp = cd.cpar + ((size_t)c * nt + n) * NCP;
+            T* cp = cd.cpar + ((size_t)n * cd.nc + c) * NCP;
             eq_cell(r0, U0, V0, l0, cd.lam0, cd.pr, qx, qy, cp + C_EQ0);
             eq_cell(r1, U1, V1, l1, cd.lam0, cd.pr, qx, qy, cp + C_EQ1);
             const double D = 1.0 + 0.5 * dG / t1;

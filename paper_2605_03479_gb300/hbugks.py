@@ -256,7 +256,7 @@ class Solver:
         return tx.value, ty.value
 
     def set_tile_shape(self, case_index: int, tx: int, ty: int) -> None:
-        """Pin the micro-update tile of a case (4x4, 4x2 or 2x2)."""
+        """Pin the micro-update tile of a case (4x4, 4x2, 2x2 or 8x4)."""
         _check(lib().hbugks_set_tile_shape(self.h, case_index, tx, ty), "set_tile_shape")
 
     # ------------------------------------------------------------------ fields

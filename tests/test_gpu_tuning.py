@@ -7,7 +7,7 @@ from paper_2605_03479_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(4, 4), (4, 2), (2, 2)]
+SHAPES = [(4, 4), (4, 2), (2, 2), (8, 4)]
 
 
 @pytest.fixture(scope="module")
@@ -27,11 +27,15 @@ def test_every_tile_gives_the_same_iterate(hb, precision):
     assert s.tile_shape(0) in SHAPES
     results = []
     for tx, ty in SHAPES:
-        s.set_tile_shape(0, tx, ty)
+        try:
+            s.set_tile_shape(0, tx, ty)
+        except hb.HbugksError:
+            continue                     # the tile needs more shared memory than a CTA may have
         assert s.tile_shape(0) == (tx, ty)
         s.set_state(0, *state)
         s.iterate(6)
         results.append(s.get_state(0))
+    assert len(results) >= 3
     for other in results[1:]:
         for a, b in zip(results[0], other):
             assert np.array_equal(a, b)
