@@ -158,6 +158,9 @@ HBUGKS_API long long hbugks_iteration_count(hbugks_t h, int case_index);
 /* Human-readable name of a status. */
 HBUGKS_API const char* hbugks_status_string(hbugks_status s);
 
+/* Description of the CUDA error behind the last HBUGKS_ECUDA returned on the calling thread. */
+HBUGKS_API const char* hbugks_cuda_error_string(void);
+
 /* Kernel-level timing support: enqueue `n` iterations on the handle's stream without any host
  * synchronisation or residual check (for timing with CUDA events around the call). */
 HBUGKS_API hbugks_status hbugks_enqueue_iterations(hbugks_t h, int n);

@@ -94,7 +94,7 @@ size_t k4_smem_of(int shape, int nt)
     }
 }
 
-constexpr size_t SMEM_MAX = 226 * 1024;   // dynamic shared memory per CTA, leaving room for static
+constexpr size_t SMEM_MAX = 219 * 1024;   // dynamic shared memory per CTA, leaving room for the static arrays
 
 // largest tile whose shared memory lets two CTAs share an SM, else the largest that fits at all
 template <typename T>
@@ -1263,6 +1263,11 @@ const char* hbugks_status_string(hbugks_status s)
         case HBUGKS_TIMEOUT: return "device wait timed out";
     }
     return "unknown status";
+}
+
+const char* hbugks_cuda_error_string(void)
+{
+    return cudaGetErrorString(last_cuda_error());
 }
 
 }  // extern "C"

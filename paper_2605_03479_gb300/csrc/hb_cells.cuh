@@ -211,13 +211,13 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
         const int vb0 = k * G, gk = min(G, nvb - vb0);
         if (valid) {
             for (int g = 0; g < gk; ++g) {
-                const int cls = vcls[vb0 + g];
+                const int cls = __ldg(vcls + vb0 + g);
                 if (cls != cur) {
                     if (cur >= 0) flush();
                     cur = cls;
                 }
                 const int a = (vb0 + g) * VB + lane;
-                const T u = tu[a], v = tv[a], w = tw[a];
+                const T u = __ldg(tu + a), v = __ldg(tv + a), w = __ldg(tw + a);
                 const T* ph = cb + (size_t)(2 * g) * blk + (size_t)kc * VB + lane;
                 const T* pb = ph + blk;
                 const T f0 = ph[0], g0 = pb[0];

@@ -24,7 +24,8 @@ FIELD_NAMES = ("rho", "U", "V", "T", "tau_xy", "qx", "qy", "p")
 
 class HbugksError(RuntimeError):
     def __init__(self, status: int, what: str):
-        super().__init__(f"{what}: {status_string(status)} ({status})")
+        detail = f" [{lib().hbugks_cuda_error_string().decode()}]" if status == ECUDA else ""
+        super().__init__(f"{what}: {status_string(status)} ({status}){detail}")
         self.status = status
 
 
@@ -59,7 +60,7 @@ EXPORTED = ("hbugks_workspace_bytes", "hbugks_create", "hbugks_destroy", "hbugks
             "hbugks_residual_history", "hbugks_get_level_fields", "hbugks_get_harmonic", "hbugks_iteration_count",
             "hbugks_status_string", "hbugks_enqueue_iterations", "hbugks_profile_kernels",
             "hbugks_harmonic_noalloc", "hbugks_launches_per_iteration", "hbugks_get_tile_shape",
-            "hbugks_set_tile_shape")
+            "hbugks_set_tile_shape", "hbugks_cuda_error_string")
 
 
 def lib():
@@ -95,11 +96,13 @@ def lib():
             L.hbugks_profile_kernels.argtypes = [vp, i, pd]
             L.hbugks_harmonic_noalloc.argtypes = [i, i, i, i, vp, vp, vp, vp, i, vp, vp, i, vp, vp, vp]
             L.hbugks_launches_per_iteration.argtypes = [vp]
+            L.hbugks_cuda_error_string.argtypes = []
+            L.hbugks_cuda_error_string.restype = C.c_char_p
             L.hbugks_get_tile_shape.argtypes = [vp, i, C.POINTER(i), C.POINTER(i)]
             L.hbugks_set_tile_shape.argtypes = [vp, i, i, i]
             for name in EXPORTED:
                 if name not in ("hbugks_workspace_bytes", "hbugks_destroy", "hbugks_iteration_count",
-                                "hbugks_status_string"):
+                                "hbugks_status_string", "hbugks_cuda_error_string"):
                     getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
