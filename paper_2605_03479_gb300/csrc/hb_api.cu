@@ -68,12 +68,13 @@ struct HostCase {
 // K1 tile (TX x TY cells, one warp each) and velocity blocks staged per pass, per storage precision
 template <typename T> constexpr int K1_TX = 4;
 template <typename T> constexpr int K1_TY = std::is_same<T, float>::value ? 4 : 2;
-template <typename T> constexpr int K1_G = std::is_same<T, float>::value ? 8 : 6;
+template <typename T> constexpr int K1_G = std::is_same<T, float>::value ? 6 : 4;
+template <typename T> constexpr int K1_S = 3;   // pipeline stages of the staged velocity blocks
 
 template <typename T>
 constexpr size_t k1_smem_of()
 {
-    return k1_cells_smem<T, K1_TX<T>, K1_TY<T>, K1_G<T>>();
+    return k1_cells_smem<T, K1_TX<T>, K1_TY<T>, K1_G<T>, K1_S<T>>();
 }
 
 // K4 tile shapes (TX, TY, warps per CTA)
@@ -549,7 +550,7 @@ __global__ void k_begin_call(CaseStatus* st, int ncases)
 template <typename T>
 void launch_k1(int total, size_t smem, Batch<T> b, cudaStream_t s)
 {
-    k1_cells<T, K1_TX<T>, K1_TY<T>, K1_G<T>><<<total, K1_TX<T> * K1_TY<T> * 32, smem, s>>>(b);
+    k1_cells<T, K1_TX<T>, K1_TY<T>, K1_G<T>, K1_S<T>><<<total, K1_TX<T> * K1_TY<T> * 32, smem, s>>>(b);
 }
 
 template <typename T>
@@ -568,7 +569,7 @@ template <typename T>
 cudaError_t set_smem_attributes()
 {
     const int big = (int)SMEM_MAX;
-    cudaError_t e = cudaFuncSetAttribute(k1_cells<T, K1_TX<T>, K1_TY<T>, K1_G<T>>,
+    cudaError_t e = cudaFuncSetAttribute(k1_cells<T, K1_TX<T>, K1_TY<T>, K1_G<T>, K1_S<T>>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k1_smem_of<T>());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k4_cells<T, 4, 4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k4_cells<T, 4, 2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);

@@ -124,12 +124,12 @@ __device__ __forceinline__ T lane_totals(T (&v)[N], int lane)
 // A wall face takes 0..12 and 18..22 from the velocities moving into the wall only and 13..17 from all.
 // Half-face slots per (cell, level): 0 x-face of the u > 0 class (the right face), 1 u < 0 (left face),
 // 2 v > 0 (top face), 3 v < 0 (bottom face).
-template <typename T, int TX, int TY, int G>
+template <typename T, int TX, int TY, int G, int S>
 __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
 {
     constexpr int PX = TX + 2, PY = TY + 2, NR = PX * PY, NWC = TX * TY;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ uint64_t bars[2];
+    __shared__ uint64_t bars[S];
     __shared__ T sacc[NWC][4][NM];
     const int cs = find_case(B.off, B.ncases, blockIdx.x);
     const CaseDev<T>& cd = B.cases[cs];
@@ -143,8 +143,8 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
     const int ti = warp % TX, tj = warp / TX, i = i0 + ti, j = j0 + tj;
     const bool valid = i < nx && j < ny;
     for (int k = lane; k < 4 * NM; k += 32) sacc[warp][k / NM][k % NM] = T(0);
-    mbar_setup(bars, 2);
-    // staged rectangle: columns i0-1 .. i0+TX, rows j0-1 .. j0+TY; buffers [2][G][h, b][NR][32]
+    mbar_setup(bars, S);
+    // staged rectangle: columns i0-1 .. i0+TX, rows j0-1 .. j0+TY; S buffers [G][h, b][NR][32] in a ring
     constexpr size_t blk = (size_t)NR * VB;
     T* buf = reinterpret_cast<T*>(smem_raw);
     const int p = cd.st->parity;
@@ -160,8 +160,8 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
     int* err = cd.err;
     auto issue = [&](int k) {
         const int vb0 = k * G, gk = min(G, nvb - vb0);
-        T* dst = buf + (size_t)(k & 1) * G * 2 * blk;
-        if (lane == 0) mbar_arrive_expect(&bars[k & 1], (uint32_t)(2 * gk) * rbytes);
+        T* dst = buf + (size_t)(k % S) * G * 2 * blk;
+        if (lane == 0) mbar_arrive_expect(&bars[k % S], (uint32_t)(2 * gk) * rbytes);
         __syncwarp();
         for (int q = lane; q < gk * 2 * PY; q += 32) {
             const int r = q % PY, ga = q / PY;   // ga = 2 g + array
@@ -169,10 +169,11 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
             if (jj < 0 || jj >= ny) continue;
             const size_t src = ((size_t)(vb0 + (ga >> 1)) * nt + n) * nc * VB + ((size_t)jj * nx + c0) * VB;
             bulk_g2s(dst + (size_t)ga * blk + (size_t)(r * PX + c0 - (i0 - 1)) * VB, ((ga & 1) ? gb : gh) + src,
-                     (uint32_t)((c1 - c0) * VB * sizeof(T)), &bars[k & 1]);
+                     (uint32_t)((c1 - c0) * VB * sizeof(T)), &bars[k % S]);
         }
     };
-    if (warp == 0) issue(0);
+    if (warp == 0)
+        for (int k = 0; k < S - 1 && k < nchunk; ++k) issue(k);
 
     // the warp's cell: neighbours, spacings, half widths (uniform over the warp)
     const bool hm = i > 0, hp = i < nx - 1, vm = j > 0, vp = j < ny - 1, sx = nx > 1, sy = ny > 1;
@@ -204,10 +205,10 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
     };
 
     for (int k = 0; k < nchunk; ++k) {
-        if (warp == 0 && k + 1 < nchunk) issue(k + 1);
-        const int fail = !mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), err);
+        if (warp == 0 && k + S - 1 < nchunk) issue(k + S - 1);
+        const int fail = !mbar_wait(&bars[k % S], (uint32_t)((k / S) & 1), err);
         if (__syncthreads_or(fail)) return;
-        const T* cb = buf + (size_t)(k & 1) * G * 2 * blk;
+        const T* cb = buf + (size_t)(k % S) * G * 2 * blk;
         const int vb0 = k * G, gk = min(G, nvb - vb0);
         if (valid) {
             for (int g = 0; g < gk; ++g) {
@@ -268,10 +269,10 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
     for (int k = lane; k < 4 * NM; k += 32) hmo[k] = (double)sacc[warp][k / NM][k % NM];
 }
 
-template <typename T, int TX, int TY, int G>
+template <typename T, int TX, int TY, int G, int S>
 constexpr size_t k1_cells_smem()
 {
-    return (size_t)2 * G * 2 * (TX + 2) * (TY + 2) * VB * sizeof(T);
+    return (size_t)S * G * 2 * (TX + 2) * (TY + 2) * VB * sizeof(T);
 }
 
 // ------------------------------------------------------------------------------ K4: micro update
