@@ -124,7 +124,7 @@ HBUGKS_API hbugks_status hbugks_set_wall(hbugks_t h, int case_index, int wall, c
 HBUGKS_API hbugks_status hbugks_init_uniform(hbugks_t h, int case_index, double rho, double u, double v, double T);
 
 /* Copy a state in (set) or out (get), canonical FP64 layout, host pointers (see top of file).
- * Sizes in doubles: W nt*nc*4, h and b nt*nc*nu*nv each. */
+ * Sizes in doubles: W nt*nc*4, h and b nt*nc*nu*nv each.  get: hh and bb may both be NULL to read W only. */
 HBUGKS_API hbugks_status hbugks_set_state(hbugks_t h, int case_index, const double* W, const double* hh, const double* bb);
 HBUGKS_API hbugks_status hbugks_get_state(hbugks_t h, int case_index, double* W, double* hh, double* bb);
 

@@ -983,7 +983,7 @@ hbugks_status hbugks_set_state(hbugks_t h, int ci, const double* W, const double
 
 hbugks_status hbugks_get_state(hbugks_t h, int ci, double* W, double* hh, double* bb)
 {
-    if (!h || ci < 0 || ci >= h->ncases || !W || !hh || !bb) return HBUGKS_EINVAL;
+    if (!h || ci < 0 || ci >= h->ncases || !W || (!hh != !bb)) return HBUGKS_EINVAL;
     return dispatch(h, [&](auto& im) -> hbugks_status {
         auto& d = im.dc[ci];
         using TT = std::remove_const_t<typename std::remove_pointer<decltype(d.tu)>::type>;
@@ -995,7 +995,7 @@ hbugks_status hbugks_get_state(hbugks_t h, int ci, double* W, double* hh, double
         HB_CK(cudaMemcpyAsync(W, d.W[st.parity], sizeof(double) * d.nt * d.nc * 4, cudaMemcpyDeviceToHost, h->s));
         const size_t lvl = (size_t)d.nc * d.nvel;
         const size_t tot = (size_t)d.nc * d.nvb * VB;
-        for (int n = 0; n < d.nt; ++n)
+        for (int n = 0; hh && n < d.nt; ++n)
             for (int which = 0; which < 2; ++which) {
                 k_get_level<TT><<<(unsigned)((tot + 255) / 256), 256, 0, h->s>>>(d, n, which, d.stage);
                 double* dst = (which == 0 ? hh : bb) + (size_t)n * lvl;

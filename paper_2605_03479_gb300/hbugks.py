@@ -217,6 +217,13 @@ class Solver:
         _check(lib().hbugks_get_state(self.h, case_index, _dp(W), _dp(h), _dp(b)), "hbugks_get_state")
         return W, h, b
 
+    def get_W(self, case_index: int = 0) -> np.ndarray:
+        """Conservative variables W[level][cell][4] only (no copy of the distributions)."""
+        c = self.cases[case_index]
+        W = np.zeros((c.nt, c.nc, 4))
+        _check(lib().hbugks_get_state(self.h, case_index, _dp(W), None, None), "hbugks_get_state")
+        return W
+
     # ------------------------------------------------------------------ iteration
     def iterate(self, max_iters: int, tol_rho: float = 0.0):
         """Returns (status, iterations per case, last residual per case (ncases, 4))."""

@@ -5,6 +5,8 @@ Tolerances (written here, derived in the design doc):
     iterations made (|gpu - oracle| <= 1e-10 max|oracle - initial| + 1e-13 max|oracle|).
   * FP32-split path: h, b, W within 2e-5 of the change plus 2e-7 of the magnitude after a few iterations;
     macroscopic fields per harmonic within 1e-5 relative at convergence (test_gpu_convergence.py).
+Edge cases: ragged tiles, a single cell, a one-cell column or row, N_H = 0 and the largest N_H = 7, odd
+velocity grids with zero nodes, the harmonic-mean face step.
 """
 import numpy as np
 import pytest
@@ -57,6 +59,15 @@ CASES_FP64 = [
                                          ncell_y=1), 6),
     ("harmonic_face_step", lambda: _with(I.make_case("g", 6, 8, kn=0.1, st=1.0, nh=1, pr=2 / 3,
                                                      stretched_ratio=1.1, drive="shear"), face_step=1), 6),
+    # odd grids: the nodes u = 0 and v = 0 (ties at every face, parallel to every wall) are stored in two sign
+    # classes with half weight each, (0, 0) in four with a quarter
+    ("zero_velocity_nodes", lambda: I.make_case("z", 7, 9, kn=0.2, st=1.0, nh=1, pr=2 / 3, drive="thermal",
+                                                amp=0.3, nvel_y=11, ncell_y=6), 6),
+    ("max_levels_nh7", lambda: I.make_case("m", 5, 8, kn=0.1, st=2.0, nh=7, pr=2 / 3, drive="thermal",
+                                           amp=0.3, ncell_y=4), 4),
+    ("single_cell", lambda: I.make_case("s", 1, 10, kn=0.5, st=1.0, nh=2, pr=2 / 3, drive="shear", amp=0.05), 6),
+    ("one_cell_column", lambda: I.make_case("k", 1, 8, kn=0.2, st=1.0, nh=1, pr=2 / 3, drive="thermal",
+                                            amp=0.3, ncell_y=5), 6),
 ]
 
 
