@@ -33,13 +33,27 @@ UNIT = "updates/s"
 
 
 def workloads():
+    """Workload name -> factory of the list of cases iterated together by one handle."""
     from paper_2605_03479_gb300 import inputs as I
     return {
-        "thermal128_v64_nh5_fp32split": lambda: I.config5(precision=1),
-        "thermal128_v64_nh5_fp64": lambda: I.config5(precision=0),
-        "thermal64_v48_nh3_fp32split": lambda: I.config3(precision=1),
-        "shear32_v24_nh1_fp64": I.config1,
+        "thermal128_v64_nh5_fp32split": lambda: [I.config5(precision=1)],
+        "thermal128_v64_nh5_fp64": lambda: [I.config5(precision=0)],
+        "thermal64_v48_nh3_fp32split": lambda: [I.config3(precision=1)],
+        "thermal64_v48_nh3_fp64": lambda: [I.config3(precision=0)],
+        "shear32_v24_nh1_fp64": lambda: [I.config1()],
+        "shear64tanh_v32_nh1_sweep12_fp64": lambda: I.config2_cases(),
+        "batch48_fp32split": lambda: I.config4_cases(precision=1),
     }
+
+
+def with_precision(cases, precision):
+    import copy
+    out = []
+    for c in cases:
+        d = copy.deepcopy(c)
+        d.precision = precision
+        out.append(d)
+    return out
 
 
 def peaks():
@@ -129,6 +143,72 @@ def run_oracle(case_full, steps, warmup, min_seconds=0.0):
     return ups, dt / n, sample
 
 
+def slowest_rank_ms(ms: float, dist, device) -> float:
+    """The job's step time: the maximum over ranks (every rank runs a replica; the job ends with the slowest)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_updates_per_s(updates_per_rank_step: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the updates of all ranks per step over the slowest rank's step time."""
+    return updates_per_rank_step * world / (ms * 1e-3)
+
+
+def describe(name, cases, upd, world):
+    par = f"replicas{world}" if world > 1 else "single"
+    if len(cases) == 1:
+        c = cases[0]
+        return {"workload": name, "cells": [c.nx, c.ny], "velocities": [c.nu, c.nv], "n_levels": c.nt, "kn": c.kn,
+                "st": c.st, "pr": c.pr, "updates_per_step": upd, "parallelism": par,
+                "l2": "state larger than L2 (no flush needed)"}
+    return {"workload": name, "cases": len(cases), "cells": sorted({c.nx for c in cases}),
+            "velocities": sorted({c.nu for c in cases}), "n_levels": sorted({c.nt for c in cases}),
+            "kn": [min(c.kn for c in cases), max(c.kn for c in cases)],
+            "st": [min(c.st for c in cases), max(c.st for c in cases)], "updates_per_step": upd,
+            "parallelism": par, "l2": "state larger than L2 (no flush needed)"}
+
+
+def time_to_residual(args, cases):
+    """Wall-clock time until every case's level-0 density residual is <= args.ttr, FP32-split and FP64 GPU
+    paths from the same start (rest), with the iteration counts.  A path that has not converged within the
+    budget is extrapolated from its own time per iteration and the other path's iteration count (the two
+    paths follow the same residual history), and flagged so."""
+    import numpy as np
+    import torch
+    from paper_2605_03479_gb300 import hbugks as hb
+    res_out = {}
+    for prec, key in ((1, "fp32split"), (0, "fp64")):
+        cs = with_precision(cases, prec)
+        s = hb.Solver(cs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = np.zeros(len(cs), dtype=np.int64)
+        while True:
+            rc, it, res = s.iterate(250, tol_rho=args.ttr)
+            its += it
+            el = time.perf_counter() - t0
+            if rc != hb.NOT_CONVERGED or el > args.ttr_budget:
+                break
+        res_out[key] = {"seconds": el, "iterations": int(its.max()), "status": hb.status_string(rc),
+                        "converged": rc == hb.OK, "residual": float(res[:, 0].max()),
+                        "seconds_per_iteration": el / max(int(its.max()), 1), "extrapolated": False}
+        s.destroy()
+    a, b = res_out["fp32split"], res_out["fp64"]
+    for x, y in ((a, b), (b, a)):
+        if not x["converged"] and y["converged"]:
+            x["seconds"] = x["seconds_per_iteration"] * y["iterations"]
+            x["extrapolated"] = True
+    line = {"metric": "time to level-0 density residual", "tol": args.ttr, "unit": "s", "workload": args.workload,
+            "cases": len(cases), "fp32split": a, "fp64": b,
+            "speedup_fp32split_over_fp64": b["seconds"] / a["seconds"] if a["seconds"] > 0 else None,
+            "higher_is_better": False, "data": "synthetic", "start": "rest on every level"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -138,12 +218,20 @@ def main():
     ap.add_argument("--workload", default="thermal128_v64_nh5_fp32split")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ttr", type=float, default=0.0,
+                    help="time to this level-0 density residual, FP32-split against FP64 (one JSON line)")
+    ap.add_argument("--ttr-budget", type=float, default=600.0, help="seconds per precision for --ttr")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    case = workloads()[args.workload]()
+    cases = workloads()[args.workload]()
+    case = cases[0]
     W_ = max(args.warmup, 3)
+    if args.ttr > 0:
+        if rank == 0:
+            time_to_residual(args, cases)
+        return
 
     if args.impl == "reference":
         if rank != 0:
@@ -170,7 +258,7 @@ def main():
     dev = f"cuda:{local}"
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    s = hb.Solver(case, device=dev, stream=stream)
+    s = hb.Solver(cases, device=dev, stream=stream)
     s.init_uniform(-1, 1.0, 0.0, 0.0, 1.0)
     s.enqueue_iterations(W_)
     torch.cuda.synchronize()
@@ -190,13 +278,9 @@ def main():
     if dist:
         dist.barrier()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    upd = case.updates_per_iteration()
-    value = upd * world / (ms * 1e-3)
+    ms = slowest_rank_ms(e0.elapsed_time(e1) / args.steps, dist, dev)
+    upd = sum(c.updates_per_iteration() for c in cases)
+    value = job_updates_per_s(upd, world, ms)
     launches = s.launches_per_iteration() * args.steps + 1
 
     # per-kernel times (CUDA events around each launch on the kernels' stream), roofline of the top kernel
@@ -217,7 +301,10 @@ def main():
     # end to end through the public API: upload the initial state from pinned host memory, iterate, read back
     # every harmonic field
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and len(cases) > 1:
+        e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+               "what": "not measured for multi-case workloads (FP64 host copies of every case's state)"}
+    elif not args.no_e2e:
         nt, nc, nv = case.nt, case.nc, case.nvel
         from paper_2605_03479_gb300 import inputs as I
         Wr, hr, br = I.initial_state(I.make_case("one", 1, case.nu, kn=case.kn, st=case.st,
@@ -252,10 +339,7 @@ def main():
                 "warmup": W_, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32-split" if case.precision == 1 else "f64",
                 "data": "synthetic",
-                "config": {"workload": args.workload, "cells": [case.nx, case.ny], "velocities": [case.nu, case.nv],
-                           "n_levels": case.nt, "kn": case.kn, "st": case.st, "pr": case.pr,
-                           "updates_per_step": upd, "parallelism": f"replicas{world}" if world > 1 else "single",
-                           "l2": "state larger than L2 (no flush needed)"},
+                "config": describe(args.workload, cases, upd, world),
                 "roofline": roof, "kernel_ms": kernel_ms, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks}
         print(json.dumps(line), flush=True)
