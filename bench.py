@@ -293,8 +293,14 @@ def main():
     roof = None
     if names[top] in alg:
         ach = alg[names[top]] * upd / (kms[top] * 1e-3) / 1e9
+        # DRAM bytes per update of the micro update (dram__bytes_read.sum + dram__bytes_write.sum of one ncu
+        # launch of k4_cells<float, 4, 4, 8> on the 64x64 / 48x48 / N_T 7 thermal cavity), scaled by updates
+        traffic = None
+        if names[top] == "micro_update" and case.precision == 1 and all(
+                s.tile_shape(k) == (4, 4) for k in range(len(cases))):
+            traffic = 17.55 * upd
         roof = {"kernel": names[top], "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_source": peak_kind, "traffic": None,
+                "frac": ach / peak, "peak_source": peak_kind, "traffic": traffic,
                 "algorithmic_bytes_per_update": alg[names[top]]}
     kernel_ms = {n: float(v) for n, v in zip(names, kms)}
 

@@ -5,7 +5,7 @@
   change + 2e-7 of the magnitude, as in test_gpu_parity.py).
 * Thermal cavity 128x128 cells, 64x64 velocities, N_T = 11 (about 6 GB of FP32-split state): the oracle needs
   minutes per iteration there, so properties that hold at any size are checked instead:
-  - a resting gas with resting walls at T0 is a fixed point (PAPER Sec 3, checked by the oracle pins);
+  - a resting gas with resting walls at T0 is a fixed point (also pinned on the oracle);
   - the cavity heated from the bottom wall is mirror-symmetric about x = 1/2 and every velocity grid used is
     symmetric, so rho, rho V, rho E are even and rho U is odd under i -> nx - 1 - i, on every level;
   - the FP32-split and FP64 paths agree on W after the same iterations.
