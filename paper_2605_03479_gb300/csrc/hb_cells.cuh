@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
 {
     constexpr int PX = TX + 2, PY = TY + 2, NR = PX * PY, NWC = TX * TY;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ uint64_t bars[S];
+    __shared__ uint64_t bars[S], empty[S];
     __shared__ T sacc[NWC][4][NM];
     const int cs = find_case(B.off, B.ncases, blockIdx.x);
     const CaseDev<T>& cd = B.cases[cs];
@@ -143,6 +143,8 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
     const int ti = warp % TX, tj = warp / TX, i = i0 + ti, j = j0 + tj;
     const bool valid = i < nx && j < ny;
     for (int k = lane; k < 4 * NM; k += 32) sacc[warp][k / NM][k % NM] = T(0);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < S; ++k) mbar_init(empty + k, NWC);   // one arrival per warp: slot read
     mbar_setup(bars, S);
     // staged rectangle: columns i0-1 .. i0+TX, rows j0-1 .. j0+TY; S buffers [G][h, b][NR][32] in a ring
     constexpr size_t blk = (size_t)NR * VB;
@@ -204,10 +206,16 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
         for (int q = 0; q < NM; ++q) { ax[q] = T(0); ay[q] = T(0); }
     };
 
+    // Ring of S slots: chunk k lands in slot k % S (mbarrier bars); each warp arrives on empty once it has
+    // read the slot, and warp 0 refills a slot only after every warp has released it, so warps run up to
+    // S - 1 chunks apart instead of meeting at a CTA barrier per chunk.
     for (int k = 0; k < nchunk; ++k) {
-        if (warp == 0 && k + S - 1 < nchunk) issue(k + S - 1);
-        const int fail = !mbar_wait(&bars[k % S], (uint32_t)((k / S) & 1), err);
-        if (__syncthreads_or(fail)) return;
+        if (warp == 0 && k + S - 1 < nchunk) {
+            const int kk = k + S - 1;
+            if (kk >= S && !mbar_wait(&empty[kk % S], (uint32_t)((kk / S - 1) & 1), err)) return;
+            issue(kk);
+        }
+        if (!mbar_wait(&bars[k % S], (uint32_t)((k / S) & 1), err)) return;
         const T* cb = buf + (size_t)(k % S) * G * 2 * blk;
         const int vb0 = k * G, gk = min(G, nvb - vb0);
         if (valid) {
@@ -257,7 +265,8 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
                 ay[22] += v * (v * syb + u * sxb) * w;
             }
         }
-        __syncthreads();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[k % S]);
     }
     if (!valid) return;
     if (cur >= 0) flush();
@@ -467,6 +476,10 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
     const int qoffy = yneg ? F_QR : F_QL, loffy = yneg ? F_LBR : F_LBL;
     int* err = cd.err;
 
+    // a tile none of whose cells touches a wall: every stencil neighbour exists
+    const bool interior = i0 >= 1 && j0 >= 1 && i0 + TX <= nx - 1 && j0 + TY <= ny - 1;
+    constexpr bool PAIRED = NCT == 2 * NW;                    // each warp owns two tile cells in pass 1
+
     for (int s = 0; s <= nt; ++s) {
         if (warp == 0 && s < nt) issue(s + 1);
         const int fail = !mbar_wait(&bars[s & 1], (uint32_t)((s >> 1) & 1), err);
@@ -479,8 +492,50 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
             const T* rh = rect + (size_t)(n & 1) * L::RECT + lane;
             const T* fpn = fps + (size_t)(n & 1) * L::FP;
             const T* ftn = ftab + n * nuv;
+            int rfirst = 0;
+            if (PAIRED && interior) {
+                // both tile cells of the warp as one straight-line block, stores last, so that the two
+                // independent chains interleave
+                T fx[2][4];
+                int sl[2][2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int it = warp + q * NW, ti = it % TX, tj = it / TX;
+                    const int i = i0 + ti, j = j0 + tj;
+                    const int kx = ti - xlo, ky = tj - ylo;
+                    const int fix = xneg ? i : i + 1, fjy = yneg ? j : j + 1;
+                    sl[q][0] = tj * (TX + 1) + fix - i0;
+                    sl[q][1] = NFX + (fjy - j0) * TX + ti;
+                    const T* tbx = ftn + (j * (nx + 1) + fix) * NTf;
+                    const T* tby = ftn + (nfx + fjy * nx + i) * NTf;
+                    const T exx = __ldg(tbx + iu), eyx = __ldg(tbx + ivn);
+                    const T exy = __ldg(tby + iu), eyy = __ldg(tby + ivn);
+                    const T* ph = rh + (ky * PX + kx) * VB;
+                    const T* pb = ph + lv;
+                    const T f0 = ph[0], g0 = pb[0];
+                    const T wxm = gxr[kx - 1], wxp = gxr[kx], wym = gyr[ky - 1], wyp = gyr[ky];
+                    const T sxh = slope(ph[-VB], f0, ph[VB], wxm, wxp, true, true, true);
+                    const T sxb = slope(pb[-VB], g0, pb[VB], wxm, wxp, true, true, true);
+                    const T syh = slope(ph[-PX * VB], f0, ph[PX * VB], wym, wyp, true, true, true);
+                    const T syb = slope(pb[-PX * VB], g0, pb[PX * VB], wym, wyp, true, true, true);
+                    const T offx = xneg ? -gxh[kx] : gxh[kx], offy = yneg ? -gyh[ky] : gyh[ky];
+                    flux_down(fpn + sl[q][0] * NP, qoff, loff, exx, eyx, href, u, v, u, v, f0 + sxh * offx,
+                              g0 + sxb * offx, sxh, syh, sxb, syb, fx[q][0], fx[q][1]);
+                    flux_down(fpn + sl[q][1] * NP, qoffy, loffy, exy, eyy, href, u, v, v, u, f0 + syh * offy,
+                              g0 + syb * offy, syh, sxh, syb, sxb, fx[q][2], fx[q][3]);
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    Fh[sl[q][0] * VB] = fx[q][0];
+                    Fb[sl[q][0] * VB] = fx[q][1];
+                    Fh[sl[q][1] * VB] = fx[q][2];
+                    Fb[sl[q][1] * VB] = fx[q][3];
+                }
+                rfirst = 2;
+            }
 #pragma unroll
             for (int r = 0; r < NPASS; ++r) {
+                if (r < rfirst) continue;
                 const int it = warp + r * NW;
                 if (it >= NIT) break;
                 int ti, tj;
