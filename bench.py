@@ -191,7 +191,8 @@ def time_to_residual(args, cases):
             rc, it, res = s.iterate(250, tol_rho=args.ttr)
             its += it
             el = time.perf_counter() - t0
-            if rc != hb.NOT_CONVERGED or el > args.ttr_budget:
+            budget = args.ttr_budget if prec == 1 or args.ttr_budget_fp64 is None else args.ttr_budget_fp64
+            if rc != hb.NOT_CONVERGED or el > budget:
                 break
         res_out[key] = {"seconds": el, "iterations": int(its.max()), "status": hb.status_string(rc),
                         "converged": rc == hb.OK, "residual": float(res[:, 0].max()),
@@ -221,6 +222,7 @@ def main():
     ap.add_argument("--ttr", type=float, default=0.0,
                     help="time to this level-0 density residual, FP32-split against FP64 (one JSON line)")
     ap.add_argument("--ttr-budget", type=float, default=600.0, help="seconds per precision for --ttr")
+    ap.add_argument("--ttr-budget-fp64", type=float, default=None, help="seconds for the FP64 path (default: same)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
