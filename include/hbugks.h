@@ -85,6 +85,13 @@ typedef struct {
     int face_step;       /* 0: min(dG_L, dG_R); 1: harmonic mean (Eq. dt_face) */
     int precision;       /* 0: FP64 everywhere; 1: FP32-split (distribution stored as FP32 deviation from
                             the T0 Maxwellian, FP64 moments, interface parameters, macro update, residual) */
+    int td_steps;        /* 0: harmonic balance (the pseudo-time iteration of Sec 2.4).  > 0: explicit
+                            time-domain UGKS on the same fluxes and walls, the scheme the paper compares
+                            HB-UGKS against (Sec 3.1, Eq. benchmark_residuals): requires n_harmonics = 0 and
+                            st > 0; every iteration is one physical step dt = 2 pi / (st td_steps) (td_steps
+                            steps per forcing period) with that global step in place of the local ones, and
+                            the walls at the phase of the step's midpoint, 2 pi (s + 1/2) / td_steps for the
+                            s-th step of a period counted from the iteration count. */
 } hbugks_physics;
 
 /* Wall waveform (Eqs. bc_vel, bc_temp): state at level n = mean + Re(amp exp(i 2 pi n / N_T)),

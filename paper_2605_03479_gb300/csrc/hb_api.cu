@@ -55,7 +55,9 @@ struct HostCase {
     int nx, ny, nu, nv, nvel, nvb, nvp, nt, nh, nfx, nf, nc;
     std::vector<double> xn, yn, u, wu, v, wv;
     double mu0, omega;
-    std::vector<double> wall_tab;   // [4][nt][3]
+    int nslot;                      // wall-state slots: nt (harmonic balance) or time steps per period
+    double dt_fixed;                // > 0: time-domain mode, the global physical step
+    std::vector<double> wall_tab;   // [4][nslot][3]
     // stored velocity order: sign classes 0 (u > 0, v > 0), 1 (u < 0, v > 0), 2 (u > 0, v < 0), 3 (u < 0, v < 0),
     // each padded to whole blocks; per slot the canonical index jv * nu + iu (-1: padding) and the share of the
     // node's weight (1/2 or 1/4 for a node with u = 0 or v = 0, stored in two or four classes)
@@ -119,14 +121,16 @@ bool validate(const hbugks_case& c)
     if (!(p.kn > 0) || !(p.cfl > 0) || !(p.st >= 0) || !(p.gamma > 0)) return false;
     if (p.precision != 0 && p.precision != 1) return false;
     if (p.face_step != 0 && p.face_step != 1) return false;
+    if (p.td_steps < 0 || (p.td_steps > 0 && (p.n_harmonics != 0 || !(p.st > 0)))) return false;
     for (int i = 0; i < m.nx; ++i) if (!(m.xnodes[i + 1] > m.xnodes[i])) return false;
     for (int j = 0; j < m.ny; ++j) if (!(m.ynodes[j + 1] > m.ynodes[j])) return false;
     for (int i = 0; i < g.nu; ++i) if (!(g.wu[i] > 0)) return false;
     for (int j = 0; j < g.nv; ++j) if (!(g.wv[j] > 0)) return false;
+    const int nslot = p.td_steps > 0 ? p.td_steps : 2 * p.n_harmonics + 1;
     for (int w = 0; w < 4; ++w) {
         const hbugks_wall& wl = c.walls[w];
-        for (int n = 0; n < 2 * p.n_harmonics + 1; ++n) {
-            double th = 2.0 * M_PI * n / (2 * p.n_harmonics + 1);
+        for (int n = 0; n < nslot; ++n) {
+            double th = p.td_steps > 0 ? 2.0 * M_PI * (n + 0.5) / nslot : 2.0 * M_PI * n / nslot;
             if (!(wl.T_mean + wl.T_re * cos(th) - wl.T_im * sin(th) > 0)) return false;
         }
     }
@@ -170,13 +174,18 @@ void fill_host(HostCase& h, const hbugks_case& c)
     const double F = 4.0 * a * (5.0 - 2.0 * w) * (7.0 - 2.0 * w) / (5.0 * (a + 1.0) * (a + 2.0));
     h.mu0 = c.phys.kn * sqrt(M_PI) / F;
     h.omega = c.phys.st;   // Eq. def_St with H = 1, sqrt(2 R T0) = 1
-    h.wall_tab.assign(4 * h.nt * 3, 0.0);
+    // wall states per level (Eqs. bc_vel, bc_temp at t_n = nT/N_T), or, in time-domain mode, per step of a
+    // period at the step's midpoint
+    const bool td = c.phys.td_steps > 0;
+    h.nslot = td ? c.phys.td_steps : h.nt;
+    h.dt_fixed = td ? 2.0 * M_PI / (h.omega * c.phys.td_steps) : 0.0;
+    h.wall_tab.assign(4 * h.nslot * 3, 0.0);
     for (int wl = 0; wl < 4; ++wl)
-        for (int n = 0; n < h.nt; ++n) {
+        for (int n = 0; n < h.nslot; ++n) {
             const hbugks_wall& W = h.src.walls[wl];
-            double th = 2.0 * M_PI * n / h.nt;
+            double th = td ? 2.0 * M_PI * (n + 0.5) / h.nslot : 2.0 * M_PI * n / h.nt;
             double cs = cos(th), sn = sin(th);
-            double* o = &h.wall_tab[(wl * h.nt + n) * 3];
+            double* o = &h.wall_tab[(wl * h.nslot + n) * 3];
             o[0] = W.u_mean + W.u_re * cs - W.u_im * sn;   // Eq. bc_vel
             o[1] = W.v_mean + W.v_re * cs - W.v_im * sn;
             o[2] = W.T_mean + W.T_re * cs - W.T_im * sn;   // Eq. bc_temp
@@ -199,7 +208,9 @@ void layout_case(Carver& cv, const HostCase& h, CaseDev<T>& d)
     for (int k = 0; k < 8; ++k) d.e[k] = 0.0;
     for (int dd = 1; dd <= h.nh; ++dd) d.e[dd] = ((dd & 1) ? -0.5 : 0.5) / sin(M_PI * dd / h.nt);   // Eq. D_explicit
     for (int k = 0; k < 8; ++k) d.et[k] = T(d.e[k]);
-    d.wall = cv.take<double>(4 * h.nt * 3);
+    d.nslot = h.nslot;
+    d.dt_fixed = h.dt_fixed;
+    d.wall = cv.take<double>((size_t)4 * h.nslot * 3);
     d.xn = cv.take<double>(h.nx + 1); d.yn = cv.take<double>(h.ny + 1);
     d.xc = cv.take<double>(h.nx); d.yc = cv.take<double>(h.ny);
     d.hx = cv.take<double>(h.nx); d.hy = cv.take<double>(h.ny);
@@ -221,14 +232,14 @@ void layout_case(Carver& cv, const HostCase& h, CaseDev<T>& d)
     d.cmom = cv.take<double>((size_t)h.nc * h.nt * NCM);
     d.fpar = cv.take<T>((size_t)h.nf * h.nt * NP);
     d.ftab = cv.take<T>((size_t)h.nf * h.nt * (h.nu + h.nv));
-    d.wtab = cv.take<T>((size_t)4 * h.nt * (h.nu + h.nv));
+    d.wtab = cv.take<T>((size_t)4 * h.nslot * (h.nu + h.nv));
     d.wxr = cv.take<T>((size_t)9 * h.nu);
     d.wyr = cv.take<T>((size_t)9 * h.nv);
     d.xr0 = cv.take<double>(36);
     d.yr0 = cv.take<double>(36);
     d.xr0t = cv.take<T>(36);
     d.yr0t = cv.take<T>(36);
-    d.wconst = cv.take<double>((size_t)4 * h.nt * WCN);
+    d.wconst = cv.take<double>((size_t)4 * h.nslot * WCN);
     d.oconst = cv.take<double>(32);
     d.ctab = cv.take<T>((size_t)h.nc * h.nt * 2 * (h.nu + h.nv));
     d.viu = cv.take<int>(h.nvp);
@@ -377,7 +388,7 @@ void fill_offsets(Impl<T>& im, int ncases)
 template <typename T>
 void wall_constants(const HostCase& h, std::vector<double>& wconst, std::vector<double>& oconst, std::vector<T>& wtab)
 {
-    const int nt = h.nt, nuv = h.nu + h.nv;
+    const int nt = h.nslot, nuv = h.nu + h.nv;      // one set per wall-state slot
     wconst.assign((size_t)4 * nt * WCN, 0.0);
     oconst.assign(32, 0.0);
     wtab.assign((size_t)4 * nt * nuv, T(0));

@@ -558,11 +558,13 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
                     if (dox) {
                         const int fi = i < 0 ? 0 : nx;
                         slot = tj * (TX + 1) + fi - i0;
-                        flux_wall(fpn + slot * NP, wtab + ((i < 0 ? 3 : 1) * nt + n) * nuv, iu, ivn, href, u, Hf, Bf);
+                        flux_wall(fpn + slot * NP, wtab + ((i < 0 ? 3 : 1) * cd.nslot + wall_slot(cd, n)) * nuv, iu,
+                                  ivn, href, u, Hf, Bf);
                     } else {
                         const int fj = j < 0 ? 0 : ny;
                         slot = NFX + (fj - j0) * TX + ti;
-                        flux_wall(fpn + slot * NP, wtab + ((j < 0 ? 0 : 2) * nt + n) * nuv, iu, ivn, href, v, Hf, Bf);
+                        flux_wall(fpn + slot * NP, wtab + ((j < 0 ? 0 : 2) * cd.nslot + wall_slot(cd, n)) * nuv, iu,
+                                  ivn, href, v, Hf, Bf);
                     }
                     Fh[slot * VB] = Hf;
                     Fb[slot * VB] = Bf;

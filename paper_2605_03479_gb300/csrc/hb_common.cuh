@@ -59,7 +59,9 @@ struct CaseDev {
     double omega, mu0, w_vss, pr, cfl, gam, umax, vmax, lam0;
     double e[8];                       // e_d = (-1)^d / (2 sin(pi d / N_T)), d = 1..N_H
     T et[8];                           // the same in the storage precision
-    const double* wall;                // [4][nt][3]  U_w, V_w, T_w per level
+    int nslot;                         // wall-state slots: nt, or time steps per period (time-domain mode)
+    double dt_fixed;                   // > 0: time-domain mode, one global physical step for every cell and face
+    const double* wall;                // [4][nslot][3]  U_w, V_w, T_w per level (per step in time-domain mode)
     const double *xn, *yn, *xc, *yc, *hx, *hy, *rdx, *rdy;   // rdx[i] = 1/(xc[i+1]-xc[i])
     const double *vu, *vv, *vw;        // per padded velocity
     const T *tu, *tv, *tw, *thref;     // per padded velocity
@@ -69,7 +71,7 @@ struct CaseDev {
     const T *wxr, *wyr;                // [9][nu], [9][nv]: w x^p exp(-lam0 x^2) per 1-D node
     const double *xr0, *yr0;           // [4][9]: sums of the above over all / positive / negative / zero nodes
     const T *xr0t, *yr0t;              // the same in the storage precision
-    const double* wconst;              // [4][nt][WCN] reflected-half constants of each wall Maxwellian
+    const double* wconst;              // [4][nslot][WCN] reflected-half constants of each wall Maxwellian
     const double* oconst;              // [4][8]: incident and reflected flux moments of (H_ref, B_ref) per wall
     T* dh[2];
     T* db[2];
@@ -79,7 +81,7 @@ struct CaseDev {
     double* cmom;                      // [nc][nt][NCM]
     T* fpar;                           // [nt][nf][NP]
     T* ftab;                           // [nf][nt][nu + nv]   expm1 factors of the interface Maxwellian
-    T* wtab;                           // [4][nt][nu + nv]  expm1 factors of each wall's Maxwellian
+    T* wtab;                           // [4][nslot][nu + nv]  expm1 factors of each wall's Maxwellian
     T* ctab;                           // [nc][nt][2][nu + nv] expm1 factors of the cell equilibria (W^k, W^{k+1})
     const int* viu;                    // per stored velocity: u index (0 for padding)
     const int* viv;                    // per stored velocity: v index
@@ -113,6 +115,14 @@ __device__ __forceinline__ int find_case(const int* off, int ncases, int blk)
         if (off[mid] <= blk) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// wall-state slot of level n in the current iteration: the level itself, or in time-domain mode the step
+// within the forcing period
+template <typename T>
+__device__ __forceinline__ int wall_slot(const CaseDev<T>& cd, int n)
+{
+    return cd.dt_fixed > 0.0 ? (int)(cd.st->iters % cd.nslot) : n;
 }
 
 __device__ __forceinline__ size_t sidx(int nc, int nt, int vb, int c, int n, int lane)

@@ -128,7 +128,8 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
     for (int k = 0; k < 13; ++k) A[k] = m[k] + cd.refmom[refset * 13 + k];
 
     // ---- diffuse wall: free-transport density estimate (Eq. rho_wall) and the mixed kinetic average
-    const double* wc = wall ? cd.wconst + ((size_t)g.wall * nt + n) * WCN : nullptr;
+    const int wsl = wall_slot(cd, n);
+    const double* wc = wall ? cd.wconst + ((size_t)g.wall * cd.nslot + wsl) * WCN : nullptr;
     double Amix[13], Dw = 1.0, rhow0 = 0.0;
 #pragma unroll
     for (int k = 0; k < 13; ++k) Amix[k] = A[k];
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
     pp[F_C5] = T(C[4] / dGf);
     pp[F_NIN] = T(nin);
     if (wall) {
-        const double* ws = cd.wall + ((size_t)g.wall * nt + n) * 3;
+        const double* ws = cd.wall + ((size_t)g.wall * cd.nslot + wsl) * 3;
         const double lamw = cd.lam0 / ws[2];
         const double rw = rhow * lamw / cd.lam0;
         pp[F_WRM1] = T(rw - 1.0);
@@ -458,7 +459,7 @@ __global__ void k_steps(Batch<T> B)
     const CaseDev<T>& cd = B.cases[cs];
     int c = (blockIdx.x - B.off[cs]) * blockDim.x + threadIdx.x;
     if (c >= cd.nc) return;
-    cd.dG[c] = local_step(cd, cd.W[cd.st->parity], c, c % cd.nx, c / cd.nx);
+    cd.dG[c] = cd.dt_fixed > 0.0 ? cd.dt_fixed : local_step(cd, cd.W[cd.st->parity], c, c % cd.nx, c / cd.nx);
 }
 
 // ------------------------------------------------------------------------------ K3 macro update
@@ -529,7 +530,7 @@ __global__ void __launch_bounds__(K3_THREADS) k3_macro(Batch<T> B)
             cp[C_KDX] = T(dG / (dx * D));
             cp[C_KDY] = T(dG / (dy * D));
         }
-        cd.dG[c] = local_step(cd, Wn, c, i, j);
+        cd.dG[c] = cd.dt_fixed > 0.0 ? cd.dt_fixed : local_step(cd, Wn, c, i, j);
     }
     // deterministic block reduction of the level-0 residual partials
     __shared__ double red[K3_THREADS][4];

@@ -49,6 +49,7 @@ class Case:
     gamma: float = 5.0 / 3.0
     face_step: int = 0          # 0 min, 1 harmonic mean
     precision: int = 0          # 0 FP64, 1 FP32-split
+    td_steps: int = 0           # > 0: explicit time-domain UGKS with this many steps per period (N_H = 0)
     walls: List[List[float]] = dataclasses.field(default_factory=lambda: [rest_wall() for _ in range(4)])
 
     @property

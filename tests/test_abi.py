@@ -60,3 +60,17 @@ def test_workspace_size_and_validation(L):
     mixed = [I.config1(), c32]                         # one handle, one precision
     assert hbugks.workspace_bytes(mixed) == 0
     assert hbugks.workspace_bytes(I.config4_cases()) > 0
+
+
+def test_time_domain_mode_needs_one_level_and_a_frequency():
+    from paper_2605_03479_gb300 import hbugks as hb
+    from paper_2605_03479_gb300 import inputs as I
+    c = I.make_case("td", 5, 8, kn=0.1, st=1.0, nh=0, drive="shear")
+    c.td_steps = 40
+    assert hb.workspace_bytes([c]) > 0
+    c.n_harmonics = 1
+    assert hb.workspace_bytes([c]) == 0
+    c.n_harmonics, c.st = 0, 0.0
+    assert hb.workspace_bytes([c]) == 0
+    c.st, c.td_steps = 1.0, -1
+    assert hb.workspace_bytes([c]) == 0
