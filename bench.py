@@ -210,6 +210,85 @@ def time_to_residual(args, cases):
     print(json.dumps(line), flush=True)
 
 
+def td_steps_per_period(c) -> int:
+    """Steps per forcing period of explicit time-domain UGKS at the case's CFL number: the largest global step
+    CFL / max_i nu_i (Eq. nu_conv at rest, u_max + sqrt(gamma R T0)), rounded so that a period holds a whole
+    number of steps."""
+    import numpy as np
+    ut = c.umax + math.sqrt(c.gamma * 0.5)
+    vt = c.vmax + math.sqrt(c.gamma * 0.5)
+    dx, dy = np.diff(c.xnodes), np.diff(c.ynodes)
+    nu = ut / dx.min() + vt / dy.min()
+    return int(math.ceil((2 * math.pi / c.st) / (c.cfl / nu)))
+
+
+def hb_versus_td(args):
+    """Wall-clock time for the density residual of Eq. benchmark_residuals to drop args.hb_vs_td orders below
+    its first valid value: HB-UGKS (R_HB over pseudo-time iterations, level 0) against explicit time-domain
+    UGKS on the same mesh, velocity grid, fluxes and walls (R_TD between consecutive periods at the same
+    phase), from rest.  The comparison the paper reports (Sec 3.1), on this GPU."""
+    import numpy as np
+    import torch
+    from paper_2605_03479_gb300 import hbugks as hb
+    from paper_2605_03479_gb300 import inputs as I
+    orders, budget = args.hb_vs_td, args.ttr_budget
+    runs = [("shear", 2.0, 1), ("shear", 30.0, 1), ("thermal", 2.0, 2), ("thermal", 30.0, 2)]
+    for drive, st, nh in runs:
+        mk = lambda h_: I.make_case(f"{drive}32_v24", 32, 24, kn=0.1, st=st, nh=h_, pr=1.0 if drive == "shear" else 2 / 3,
+                                    drive=drive, amp=0.01 if drive == "shear" else 0.3, precision=args.precision)
+        out = {}
+        # harmonic balance
+        c = mk(nh)
+        s = hb.Solver(c)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, r1, r, hist = 0, 0.0, 0.0, []
+        while True:
+            s.iterate(16)
+            its += 16
+            h_ = s.residual_history(0, 16)[:, 0]
+            if r1 == 0.0 and np.any(h_ > 0):
+                r1 = float(h_[h_ > 0][0])
+            r = float(h_[-1])
+            el = time.perf_counter() - t0
+            if (r1 > 0 and r <= r1 * 10.0 ** (-orders)) or el > budget or not np.isfinite(r):
+                break
+        out["hb"] = {"seconds": el, "iterations": its, "first_residual": r1, "residual": r,
+                     "reached": bool(r1 > 0 and r <= r1 * 10.0 ** (-orders)), "n_levels": c.nt,
+                     "updates_per_iteration": c.updates_per_iteration()}
+        s.destroy()
+        # explicit time domain
+        c = mk(0)
+        c.td_steps = M = td_steps_per_period(c)
+        s = hb.Solver(c)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prev = s.get_W(0)[0, :, 0].copy()
+        periods, r1, r = 0, 0.0, 0.0
+        while True:
+            s.iterate(M)
+            periods += 1
+            rho = s.get_W(0)[0, :, 0]
+            r = float(np.sqrt(np.mean((rho - prev) ** 2)))
+            prev = rho.copy()
+            if r1 == 0.0 and r > 0:
+                r1 = r
+            el = time.perf_counter() - t0
+            if (r1 > 0 and r <= r1 * 10.0 ** (-orders)) or el > budget or not np.isfinite(r):
+                break
+        out["td"] = {"seconds": el, "periods": periods, "steps_per_period": M, "steps": periods * M,
+                     "first_residual": r1, "residual": r, "reached": bool(r1 > 0 and r <= r1 * 10.0 ** (-orders)),
+                     "updates_per_step": c.updates_per_iteration()}
+        s.destroy()
+        line = {"metric": "wall time to a density-residual drop, HB-UGKS vs explicit time-domain UGKS",
+                "orders": orders, "unit": "s", "case": f"{drive} cavity 32x32 cells, 24x24 velocities, Kn 0.1, St {st:g}",
+                "dtype": "f32-split" if args.precision else "f64", "hb": out["hb"], "td": out["td"],
+                "speedup_hb_over_td": out["td"]["seconds"] / out["hb"]["seconds"],
+                "paper_speedup": {"shear St 2": 1.4, "shear St 30": 9.0, "thermal St 2": 1.06, "thermal St 30": 8.26},
+                "data": "synthetic", "start": "rest"}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -223,6 +302,9 @@ def main():
                     help="time to this level-0 density residual, FP32-split against FP64 (one JSON line)")
     ap.add_argument("--ttr-budget", type=float, default=600.0, help="seconds per precision for --ttr")
     ap.add_argument("--ttr-budget-fp64", type=float, default=None, help="seconds for the FP64 path (default: same)")
+    ap.add_argument("--hb-vs-td", type=float, default=0.0,
+                    help="orders of residual drop: time HB-UGKS against explicit time-domain UGKS (one JSON line per case)")
+    ap.add_argument("--precision", type=int, default=0, help="precision of --hb-vs-td (0 FP64, 1 FP32-split)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -233,6 +315,10 @@ def main():
     if args.ttr > 0:
         if rank == 0:
             time_to_residual(args, cases)
+        return
+    if args.hb_vs_td > 0:
+        if rank == 0:
+            hb_versus_td(args)
         return
 
     if args.impl == "reference":
