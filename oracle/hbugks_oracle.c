@@ -57,6 +57,8 @@ typedef struct {
     double theta0;              /* phase of level 0 in radians (0 for HB) */
     double dt_fixed;            /* > 0: one global step for every cell and face (time-domain mode) */
     int first_order;            /* 1: zero slopes (debug / test mode) */
+    int spectral_implicit;      /* 1: the spectral source at the new iterate (solved across levels per cell and
+                                   velocity); 0: at the old iterate, as printed in Eqs. fv_W, fv_h */
 } orc_problem;
 
 /* ---------------------------------------------------------------- spectral derivative matrix */
@@ -241,6 +243,31 @@ static void wall_state(const orc_problem *P, int wall, int n, double *Uw, double
 }
 
 /* ------------------------------------------------------------------- local pseudo-time steps */
+
+/* Solve A x = r in place (r becomes x) for an n x n matrix A (row-major, overwritten): Gaussian elimination with
+ * partial pivoting, the textbook algorithm. */
+static void solve_dense(int n, double* A, double* r)
+{
+    for (int k = 0; k < n; k++) {
+        int piv = k;
+        for (int i = k + 1; i < n; i++)
+            if (fabs(A[i * n + k]) > fabs(A[piv * n + k])) piv = i;
+        if (piv != k) {
+            for (int j = 0; j < n; j++) { double t = A[k * n + j]; A[k * n + j] = A[piv * n + j]; A[piv * n + j] = t; }
+            double t = r[k]; r[k] = r[piv]; r[piv] = t;
+        }
+        for (int i = k + 1; i < n; i++) {
+            double f = A[i * n + k] / A[k * n + k];
+            for (int j = k; j < n; j++) A[i * n + j] -= f * A[k * n + j];
+            r[i] -= f * r[k];
+        }
+    }
+    for (int k = n - 1; k >= 0; k--) {
+        double s = r[k];
+        for (int j = k + 1; j < n; j++) s -= A[k * n + j] * r[j];
+        r[k] = s / A[k * n + k];
+    }
+}
 
 /* Eqs. dt_hb, nu_conv: dG_i = CFL / (nu_conv,i + omega N_H), one value per cell (largest nu over levels) */
 static void cell_steps(const orc_problem *P, const geom *g, const double *W, double *dG)
@@ -664,11 +691,28 @@ int orc_hb_iterate(const orc_problem *P, double *W, double *h, double *b, int ni
                     double area = g.dx[i] * g.dy[j];
                     for (int p = 0; p < 4; p++) {
                         double src = 0.0;
-                        for (int m = 0; m < nt; m++) src += E[n * nt + m] * W[((size_t)m * Nc + c) * 4 + p];
+                        if (!P->spectral_implicit)
+                            for (int m = 0; m < nt; m++) src += E[n * nt + m] * W[((size_t)m * Nc + c) * 4 + p];
                         Wn[((size_t)n * Nc + c) * 4 + p] = W[((size_t)n * Nc + c) * 4 + p]
                             - dG[c] * (divW[((size_t)n * Nc + c) * 4 + p] / area + P->omega * src);
                     }
                 }
+        if (P->spectral_implicit) {
+            /* spectral source at the new iterate: (I + dG omega E) W^{k+1} = W^k - dG div F, per cell and variable */
+            double* A = (double*)malloc(sizeof(double) * nt * nt);
+            double* r = (double*)malloc(sizeof(double) * nt);
+            for (int c = 0; c < Nc; c++)
+                for (int p = 0; p < 4; p++) {
+                    for (int n = 0; n < nt; n++) {
+                        for (int m = 0; m < nt; m++) A[n * nt + m] = (n == m ? 1.0 : 0.0) + dG[c] * P->omega * E[n * nt + m];
+                        r[n] = Wn[((size_t)n * Nc + c) * 4 + p];
+                    }
+                    solve_dense(nt, A, r);
+                    for (int n = 0; n < nt; n++) Wn[((size_t)n * Nc + c) * 4 + p] = r[n];
+                }
+            free(A);
+            free(r);
+        }
 
         /* (5) micro update with implicit collision (Eq. fv_h) */
         for (int n = 0; n < nt; n++)
@@ -693,7 +737,7 @@ int orc_hb_iterate(const orc_problem *P, double *W, double *h, double *b, int ni
                             maxwell(r1, U1, V1, l1, u, v, &H1, &B1);
                             shakhov(P, r1, U1, V1, l1, qx, qy, u, v, H1, B1, &Hp1, &Bp1);
                             double Eh = 0.0, Eb = 0.0;
-                            for (int m = 0; m < nt; m++) {
+                            for (int m = 0; m < nt && !P->spectral_implicit; m++) {
                                 size_t km = (size_t)m * NS + (size_t)c * Nv + a;
                                 Eh += E[n * nt + m] * h[km];
                                 Eb += E[n * nt + m] * b[km];
@@ -704,6 +748,37 @@ int orc_hb_iterate(const orc_problem *P, double *W, double *h, double *b, int ni
                                      + 0.5 * d * ((B1 + Bp1) / t1 + (Bk + Bpk - b[k]) / t0)) / (1.0 + 0.5 * d / t1);
                         }
                 }
+
+        if (P->spectral_implicit) {
+            /* spectral source at the new iterate: the update above divided by (1 + dG/(2 tau^{k+1})) is
+             * D h^{k+1} = rhs with D = diag(1 + dG/(2 tau_n^{k+1})); with the source it becomes
+             * (D + dG omega E) h^{k+1} = D (update above), solved per cell and velocity (same for b) */
+            double* A = (double*)malloc(sizeof(double) * nt * nt);
+            double* r = (double*)malloc(sizeof(double) * nt);
+            double* Dn = (double*)malloc(sizeof(double) * nt);
+            for (int c = 0; c < Nc; c++) {
+                for (int n = 0; n < nt; n++) {
+                    double r1, U1, V1, l1;
+                    prim(&Wn[((size_t)n * Nc + c) * 4], &r1, &U1, &V1, &l1);
+                    Dn[n] = 1.0 + 0.5 * dG[c] / relax_time(P, r1, l1);
+                }
+                for (int arr = 0; arr < 2; arr++) {
+                    double* x = arr == 0 ? hn : bn;
+                    for (int a = 0; a < Nv; a++) {
+                        for (int n = 0; n < nt; n++) {
+                            for (int m = 0; m < nt; m++)
+                                A[n * nt + m] = (n == m ? Dn[n] : 0.0) + dG[c] * P->omega * E[n * nt + m];
+                            r[n] = Dn[n] * x[(size_t)n * NS + (size_t)c * Nv + a];
+                        }
+                        solve_dense(nt, A, r);
+                        for (int n = 0; n < nt; n++) x[(size_t)n * NS + (size_t)c * Nv + a] = r[n];
+                    }
+                }
+            }
+            free(A);
+            free(r);
+            free(Dn);
+        }
 
         /* (6) level-0 residual (Eq. benchmark_residuals) */
         if (resid) {

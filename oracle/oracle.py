@@ -49,6 +49,7 @@ class OrcProblem(C.Structure):
         ("cfl", C.c_double), ("face_step", C.c_int), ("gam", C.c_double), ("lam_ref", C.c_double),
         ("wall", (C.c_double * 9) * 4),
         ("theta0", C.c_double), ("dt_fixed", C.c_double), ("first_order", C.c_int),
+        ("spectral_implicit", C.c_int),
     ]
 
 
@@ -128,6 +129,7 @@ class Problem:
             for q in range(9):
                 s.wall[k][q] = case.walls[k][q]
         s.theta0, s.dt_fixed, s.first_order = theta0, dt_fixed, int(first_order)
+        s.spectral_implicit = int(getattr(case, "spectral_implicit", 0))
         self.s = s
 
     @property

@@ -50,6 +50,7 @@ class Case:
     face_step: int = 0          # 0 min, 1 harmonic mean
     precision: int = 0          # 0 FP64, 1 FP32-split
     td_steps: int = 0           # > 0: explicit time-domain UGKS with this many steps per period (N_H = 0)
+    spectral_implicit: int = 0  # 1: spectral source at the new pseudo-time iterate (solved across levels)
     walls: List[List[float]] = dataclasses.field(default_factory=lambda: [rest_wall() for _ in range(4)])
 
     @property
