@@ -92,6 +92,12 @@ typedef struct {
                             steps per forcing period) with that global step in place of the local ones, and
                             the walls at the phase of the step's midpoint, 2 pi (s + 1/2) / td_steps for the
                             s-th step of a period counted from the iteration count. */
+    int spectral_implicit; /* 0: the spectral source at the old pseudo-time iterate, as printed in Eqs. fv_W and
+                            fv_h (forward Euler; it amplifies the modes the source rotates by about
+                            (dG omega k)^2 / 2 per iteration).  1: at the new iterate, solved across the levels
+                            of each cell (and velocity): the same fixed point, those modes damped.  The paper
+                            names an implicit HB scheme as future work (Sec 4); this is that choice for the
+                            spectral source only. */
 } hbugks_physics;
 
 /* Wall waveform (Eqs. bc_vel, bc_temp): state at level n = mean + Re(amp exp(i 2 pi n / N_T)),

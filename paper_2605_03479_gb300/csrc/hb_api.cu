@@ -122,6 +122,7 @@ bool validate(const hbugks_case& c)
     if (p.precision != 0 && p.precision != 1) return false;
     if (p.face_step != 0 && p.face_step != 1) return false;
     if (p.td_steps < 0 || (p.td_steps > 0 && (p.n_harmonics != 0 || !(p.st > 0)))) return false;
+    if (p.spectral_implicit != 0 && p.spectral_implicit != 1) return false;
     for (int i = 0; i < m.nx; ++i) if (!(m.xnodes[i + 1] > m.xnodes[i])) return false;
     for (int j = 0; j < m.ny; ++j) if (!(m.ynodes[j + 1] > m.ynodes[j])) return false;
     for (int i = 0; i < g.nu; ++i) if (!(g.wu[i] > 0)) return false;
@@ -208,6 +209,8 @@ void layout_case(Carver& cv, const HostCase& h, CaseDev<T>& d)
     for (int k = 0; k < 8; ++k) d.e[k] = 0.0;
     for (int dd = 1; dd <= h.nh; ++dd) d.e[dd] = ((dd & 1) ? -0.5 : 0.5) / sin(M_PI * dd / h.nt);   // Eq. D_explicit
     for (int k = 0; k < 8; ++k) d.et[k] = T(d.e[k]);
+    d.spectral_implicit = h.src.phys.spectral_implicit;
+    d.minv = cv.take<T>((size_t)h.nc * h.nt * h.nt);
     d.nslot = h.nslot;
     d.dt_fixed = h.dt_fixed;
     d.wall = cv.take<double>((size_t)4 * h.nslot * 3);

@@ -476,6 +476,7 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
     const int qoffy = yneg ? F_QR : F_QL, loffy = yneg ? F_LBR : F_LBL;
     int* err = cd.err;
 
+    const bool implicit = cd.spectral_implicit != 0;
     // a tile none of whose cells touches a wall: every stencil neighbour exists
     const bool interior = i0 >= 1 && j0 >= 1 && i0 + TX <= nx - 1 && j0 + TY <= ny - 1;
     constexpr bool PAIRED = NCT == 2 * NW;                    // each warp owns two tile cells in pass 1
@@ -632,10 +633,10 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
                 const T dyh = Fh[(fB + TX) * VB] - Fh[fB * VB];
                 const T dxb = Fb[(fL + 1) * VB] - Fb[fL * VB];
                 const T dyb = Fb[(fB + TX) * VB] - Fb[fB * VB];
-                const T* hc = own + ct * VB + lane;          // level m, array a at hc[m * lvo + a * NCT * VB]
-                const T* bc = hc + NCT * VB;
+                T* hc = own + ct * VB + lane;                // level m, array a at hc[m * lvo + a * NCT * VB]
+                T* bc = hc + NCT * VB;
                 T eh, eb;
-                switch (nh) {
+                switch (implicit ? 0 : nh) {
                     case 0: eh = T(0); eb = T(0); break;
                     case 1: spectral<1>(hc, bc, n, nt, lvo, et, eh, eb); break;
                     case 2: spectral<2>(hc, bc, n, nt, lvo, et, eh, eb); break;
@@ -668,11 +669,54 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
                 }
                 const T* k = cp + C_KSELF;                    // kself, kE, kp1, kp0, kdx, kdy
                 const T h0 = hc[n * lvo], b0 = bc[n * lvo];
-                on[c * VB] = k[0] * h0 - k[4] * dxh - k[5] * dyh - k[1] * eh + k[2] * dhp[1] + k[3] * dhp[0];
-                onb[c * VB] = k[0] * b0 - k[4] * dxb - k[5] * dyb - k[1] * eb + k[2] * dbp[1] + k[3] * dbp[0];
+                const T xh = k[0] * h0 - k[4] * dxh - k[5] * dyh - k[1] * eh + k[2] * dhp[1] + k[3] * dhp[0];
+                const T xb = k[0] * b0 - k[4] * dxb - k[5] * dyb - k[1] * eb + k[2] * dbp[1] + k[3] * dbp[0];
+                if (implicit) {
+                    // right-hand side of level n; h^k of this level is no longer needed
+                    hc[n * lvo] = xh;
+                    bc[n * lvo] = xb;
+                } else {
+                    on[c * VB] = xh;
+                    onb[c * VB] = xb;
+                }
             }
         }
         __syncthreads();
+    }
+    if (implicit) {
+        // spectral source at the new iterate: h^{k+1} = minv (right-hand sides over the levels), per cell and lane
+        constexpr int lvo = 2 * NCT * VB;
+        for (int ct = warp; ct < NCT; ct += NW) {
+            const int ti = ct % TX, tj = ct / TX;
+            const int i = i0 + ti, j = j0 + tj;
+            if (i >= nx || j >= ny) continue;
+            const int c = j * nx + i;
+            const T* hc = own + ct * VB + lane;
+            const T* bc = hc + NCT * VB;
+            T rh[MAXNT], rb[MAXNT];
+#pragma unroll
+            for (int m = 0; m < MAXNT; ++m) {
+                rh[m] = m < nt ? hc[m * lvo] : T(0);
+                rb[m] = m < nt ? bc[m * lvo] : T(0);
+            }
+            const T* Mi = cd.minv + (size_t)c * nt * nt;
+            T* oh = cd.dh[p ^ 1] + (size_t)vb * nt * nc * VB + (size_t)c * VB + lane;
+            T* ob = cd.db[p ^ 1] + (size_t)vb * nt * nc * VB + (size_t)c * VB + lane;
+#pragma unroll
+            for (int n = 0; n < MAXNT; ++n) {
+                if (n >= nt) break;
+                T sh = T(0), sb = T(0);
+#pragma unroll
+                for (int m = 0; m < MAXNT; ++m)
+                    if (m < nt) {
+                        const T w = __ldg(Mi + n * nt + m);
+                        sh += w * rh[m];
+                        sb += w * rb[m];
+                    }
+                oh[(size_t)n * nc * VB] = sh;
+                ob[(size_t)n * nc * VB] = sb;
+            }
+        }
     }
 }
 

@@ -59,6 +59,8 @@ struct CaseDev {
     double omega, mu0, w_vss, pr, cfl, gam, umax, vmax, lam0;
     double e[8];                       // e_d = (-1)^d / (2 sin(pi d / N_T)), d = 1..N_H
     T et[8];                           // the same in the storage precision
+    int spectral_implicit;             // spectral source at the new pseudo-time iterate
+    T* minv;                           // [nc][nt][nt] inverse of diag(1 + dG/(2 tau_n^{k+1})) + dG omega E (implicit)
     int nslot;                         // wall-state slots: nt, or time steps per period (time-domain mode)
     double dt_fixed;                   // > 0: time-domain mode, one global physical step for every cell and face
     const double* wall;                // [4][nslot][3]  U_w, V_w, T_w per level (per step in time-domain mode)

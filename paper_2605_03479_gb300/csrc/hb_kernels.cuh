@@ -464,6 +464,50 @@ __global__ void k_steps(Batch<T> B)
 
 // ------------------------------------------------------------------------------ K3 macro update
 
+// A = diag(D) + dG omega E (D = 1 when null), E of Eq. D_explicit from the paired offsets e_d:
+// E_{n, n-d} = e_d, E_{n, n+d} = -e_d (levels cyclic)
+template <typename T>
+__device__ void spectral_matrix(const CaseDev<T>& cd, double dG, const double* D, double (&A)[MAXNT][MAXNT])
+{
+    const int nt = cd.nt;
+    for (int n = 0; n < nt; ++n)
+        for (int m = 0; m < nt; ++m) A[n][m] = n == m ? (D ? D[n] : 1.0) : 0.0;
+    for (int n = 0; n < nt; ++n)
+        for (int d = 1; d <= cd.nh; ++d) {
+            int nm = n - d; if (nm < 0) nm += nt;
+            int np = n + d; if (np >= nt) np -= nt;
+            A[n][nm] += dG * cd.omega * cd.e[d];
+            A[n][np] -= dG * cd.omega * cd.e[d];
+        }
+}
+
+// Solve A X = R in place for the columns of R (R becomes X), A destroyed: Gaussian elimination with partial
+// pivoting over the levels
+template <int NR>
+__device__ void solve_levels(int nt, double (&A)[MAXNT][MAXNT], double (&R)[MAXNT][NR])
+{
+    for (int k = 0; k < nt; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < nt; ++i)
+            if (fabs(A[i][k]) > fabs(A[piv][k])) piv = i;
+        if (piv != k) {
+            for (int j = 0; j < nt; ++j) { const double t = A[k][j]; A[k][j] = A[piv][j]; A[piv][j] = t; }
+            for (int j = 0; j < NR; ++j) { const double t = R[k][j]; R[k][j] = R[piv][j]; R[piv][j] = t; }
+        }
+        for (int i = k + 1; i < nt; ++i) {
+            const double f = A[i][k] / A[k][k];
+            for (int j = k; j < nt; ++j) A[i][j] -= f * A[k][j];
+            for (int j = 0; j < NR; ++j) R[i][j] -= f * R[k][j];
+        }
+    }
+    for (int k = nt - 1; k >= 0; --k)
+        for (int j = 0; j < NR; ++j) {
+            double s = R[k][j];
+            for (int m = k + 1; m < nt; ++m) s -= A[k][m] * R[m][j];
+            R[k][j] = s / A[k][k];
+        }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(K3_THREADS) k3_macro(Batch<T> B)
 {
@@ -486,6 +530,24 @@ __global__ void __launch_bounds__(K3_THREADS) k3_macro(Batch<T> B)
         for (int n = 0; n < nt; ++n)
 #pragma unroll
             for (int k = 0; k < 4; ++k) Wc[n][k] = W[((size_t)n * nc + c) * 4 + k];
+        const bool implicit = cd.spectral_implicit != 0;
+        double Wi[MAXNT][4];
+        if (implicit) {
+            // spectral source at the new iterate: (I + dG omega E) W^{k+1} = W^k - dG div F for every variable
+            double A[MAXNT][MAXNT];
+            spectral_matrix(cd, dG, nullptr, A);
+            for (int n = 0; n < nt; ++n) {
+                const double* FL = cd.fflux + ((size_t)fL * nt + n) * 4;
+                const double* FR = cd.fflux + ((size_t)fR * nt + n) * 4;
+                const double* FB = cd.fflux + ((size_t)fB * nt + n) * 4;
+                const double* FT = cd.fflux + ((size_t)fT * nt + n) * 4;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    Wi[n][k] = Wc[n][k] - dG * (dy * (FR[k] - FL[k]) + dx * (FT[k] - FB[k])) / area;
+            }
+            solve_levels(nt, A, Wi);
+        }
+        double Dn[MAXNT];
         for (int n = 0; n < nt; ++n) {
             const double* FL = cd.fflux + ((size_t)fL * nt + n) * 4;
             const double* FR = cd.fflux + ((size_t)fR * nt + n) * 4;
@@ -494,14 +556,18 @@ __global__ void __launch_bounds__(K3_THREADS) k3_macro(Batch<T> B)
             double wn[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                double div = (dy * (FR[k] - FL[k]) + dx * (FT[k] - FB[k])) / area;
-                double ew = 0.0;
-                for (int d = 1; d <= cd.nh; ++d) {
-                    int nm = n - d; if (nm < 0) nm += nt;
-                    int np = n + d; if (np >= nt) np -= nt;
-                    ew += cd.e[d] * (Wc[nm][k] - Wc[np][k]);
+                if (implicit) {
+                    wn[k] = Wi[n][k];
+                } else {
+                    double div = (dy * (FR[k] - FL[k]) + dx * (FT[k] - FB[k])) / area;
+                    double ew = 0.0;
+                    for (int d = 1; d <= cd.nh; ++d) {
+                        int nm = n - d; if (nm < 0) nm += nt;
+                        int np = n + d; if (np >= nt) np -= nt;
+                        ew += cd.e[d] * (Wc[nm][k] - Wc[np][k]);
+                    }
+                    wn[k] = Wc[n][k] - dG * (div + cd.omega * ew);
                 }
-                wn[k] = Wc[n][k] - dG * (div + cd.omega * ew);
                 Wn[((size_t)n * nc + c) * 4 + k] = wn[k];
             }
             if (n == 0) {
@@ -522,13 +588,28 @@ __global__ void __launch_bounds__(K3_THREADS) k3_macro(Batch<T> B)
             T* cp = cd.cpar + ((size_t)n * cd.nc + c) * NCP;
             eq_cell(r0, U0, V0, l0, cd.lam0, cd.pr, qx, qy, cp + C_EQ0);
             eq_cell(r1, U1, V1, l1, cd.lam0, cd.pr, qx, qy, cp + C_EQ1);
+            // explicit: the update of Eq. fv_h divided by D; implicit: its right-hand side, which the micro
+            // update then multiplies by minv across levels
             const double D = 1.0 + 0.5 * dG / t1;
-            cp[C_KSELF] = T((1.0 - 0.5 * dG / t0) / D);
-            cp[C_KE] = T(dG * cd.omega / D);
-            cp[C_KP1] = T(0.5 * dG / (t1 * D));
-            cp[C_KP0] = T(0.5 * dG / (t0 * D));
-            cp[C_KDX] = T(dG / (dx * D));
-            cp[C_KDY] = T(dG / (dy * D));
+            Dn[n] = D;
+            const double s_ = implicit ? 1.0 : D;
+            cp[C_KSELF] = T((1.0 - 0.5 * dG / t0) / s_);
+            cp[C_KE] = T(implicit ? 0.0 : dG * cd.omega / D);
+            cp[C_KP1] = T(0.5 * dG / (t1 * s_));
+            cp[C_KP0] = T(0.5 * dG / (t0 * s_));
+            cp[C_KDX] = T(dG / (dx * s_));
+            cp[C_KDY] = T(dG / (dy * s_));
+        }
+        if (implicit) {
+            // inverse of diag(D_n) + dG omega E for the micro update of this cell (every velocity)
+            double A[MAXNT][MAXNT], X[MAXNT][MAXNT];
+            spectral_matrix(cd, dG, Dn, A);
+            for (int n = 0; n < nt; ++n)
+                for (int m = 0; m < nt; ++m) X[n][m] = n == m ? 1.0 : 0.0;
+            solve_levels(nt, A, X);
+            T* mo = cd.minv + (size_t)c * nt * nt;
+            for (int n = 0; n < nt; ++n)
+                for (int m = 0; m < nt; ++m) mo[n * nt + m] = T(X[n][m]);
         }
         cd.dG[c] = cd.dt_fixed > 0.0 ? cd.dt_fixed : local_step(cd, Wn, c, i, j);
     }

@@ -43,7 +43,8 @@ class VGrid(C.Structure):
 class Physics(C.Structure):
     _fields_ = [("kn", C.c_double), ("st", C.c_double), ("pr", C.c_double), ("cfl", C.c_double),
                 ("w_vss", C.c_double), ("alpha_vss", C.c_double), ("gamma", C.c_double),
-                ("n_harmonics", C.c_int), ("face_step", C.c_int), ("precision", C.c_int), ("td_steps", C.c_int)]
+                ("n_harmonics", C.c_int), ("face_step", C.c_int), ("precision", C.c_int), ("td_steps", C.c_int),
+                ("spectral_implicit", C.c_int)]
 
 
 class Wall(C.Structure):
@@ -133,7 +134,8 @@ class _CaseArgs:
         c.mesh = Mesh(len(xn) - 1, len(yn) - 1, _dp(xn), _dp(yn))
         c.vgrid = VGrid(len(u), len(v), _dp(u), _dp(wu), _dp(v), _dp(wv), case.umax, case.vmax)
         c.phys = Physics(case.kn, case.st, case.pr, case.cfl, case.w_vss, case.alpha_vss, case.gamma,
-                         case.n_harmonics, case.face_step, case.precision, case.td_steps)
+                         case.n_harmonics, case.face_step, case.precision, case.td_steps,
+                         case.spectral_implicit)
         for k in range(4):
             c.walls[k] = Wall(*[float(x) for x in case.walls[k]])
         self.c = c

@@ -191,3 +191,25 @@ def test_iterate_to_residual_stops_and_reports(hb):
     assert res[0, 0] <= 1e-9 and its[0] >= 10
     hist = s.residual_history(0, 5)
     assert hist[-1, 0] == res[0, 0]
+
+
+# spectral source at the new pseudo-time iterate (hbugks_physics.spectral_implicit = 1) against the oracle's
+# same option: the macro update solves (I + dG omega E) across levels per cell, the micro update applies the
+# inverse of diag(D) + dG omega E per cell to every velocity
+IMPLICIT = [CASES_FP64[0], CASES_FP64[2], CASES_FP64[3], CASES_FP64[-4], CASES_FP64[-3]]
+
+
+@pytest.mark.parametrize("name,factory,niter", IMPLICIT, ids=[c[0] for c in IMPLICIT])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_implicit_spectral_matches_oracle(hb, name, factory, niter, precision):
+    case = factory()
+    case.spectral_implicit = 1
+    case.precision = precision
+    init, g, o, res_g, res_o = run_both(hb, case, niter)
+    if precision == 0:
+        for k in range(3):
+            close(g[k], o[k], init[k], 1e-10, 1e-13)
+    else:
+        close(g[0], o[0], init[0], 2e-5, 2e-9)
+        close(g[1], o[1], init[1], 2e-5, 2e-7)
+        close(g[2], o[2], init[2], 2e-5, 2e-7)
