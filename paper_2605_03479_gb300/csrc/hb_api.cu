@@ -284,6 +284,7 @@ struct Impl {
     std::vector<int> off_host;
     std::vector<LaunchSpec> specs;   // in launch order (without the residual kernel)
     int k3_table = 0, steps_table = 0;
+    bool any_implicit = false;       // some case takes the spectral source at the new iterate
 };
 
 struct hbugks_solver {
@@ -567,15 +568,23 @@ void launch_k1(int total, size_t smem, Batch<T> b, cudaStream_t s)
     k1_cells<T, K1_TX<T>, K1_TY<T>, K1_G<T>, K1_S<T>><<<total, K1_TX<T> * K1_TY<T> * 32, smem, s>>>(b);
 }
 
-template <typename T>
-void launch_k4(int shape, int total, size_t smem, Batch<T> b, cudaStream_t s)
+template <typename T, bool IMP>
+void launch_k4_(int shape, int total, size_t smem, Batch<T> b, cudaStream_t s)
 {
     switch (shape) {
-        case 0: k4_cells<T, 4, 4, 8><<<total, 8 * 32, smem, s>>>(b); break;
-        case 1: k4_cells<T, 4, 2, 8><<<total, 8 * 32, smem, s>>>(b); break;
-        case 2: k4_cells<T, 2, 2, 4><<<total, 4 * 32, smem, s>>>(b); break;
-        default: k4_cells<T, 8, 4, 16><<<total, 16 * 32, smem, s>>>(b); break;
+        case 0: k4_cells<T, 4, 4, 8, IMP><<<total, 8 * 32, smem, s>>>(b); break;
+        case 1: k4_cells<T, 4, 2, 8, IMP><<<total, 8 * 32, smem, s>>>(b); break;
+        case 2: k4_cells<T, 2, 2, 4, IMP><<<total, 4 * 32, smem, s>>>(b); break;
+        default: k4_cells<T, 8, 4, 16, IMP><<<total, 16 * 32, smem, s>>>(b); break;
     }
+}
+
+// the explicit-only kernels unless a case of the handle takes the spectral source at the new iterate
+template <typename T>
+void launch_k4(bool imp, int shape, int total, size_t smem, Batch<T> b, cudaStream_t s)
+{
+    if (imp) launch_k4_<T, true>(shape, total, smem, b, s);
+    else launch_k4_<T, false>(shape, total, smem, b, s);
 }
 
 // every K4 shape may be chosen later (autotuning), so each gets the largest dynamic shared memory it can use
@@ -585,10 +594,13 @@ cudaError_t set_smem_attributes()
     const int big = (int)SMEM_MAX;
     cudaError_t e = cudaFuncSetAttribute(k1_cells<T, K1_TX<T>, K1_TY<T>, K1_G<T>, K1_S<T>>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k1_smem_of<T>());
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k4_cells<T, 4, 4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k4_cells<T, 4, 2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k4_cells<T, 2, 2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k4_cells<T, 8, 4, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    auto set = [&](auto k) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    };
+    set(k4_cells<T, 4, 4, 8, false>); set(k4_cells<T, 4, 2, 8, false>);
+    set(k4_cells<T, 2, 2, 4, false>); set(k4_cells<T, 8, 4, 16, false>);
+    set(k4_cells<T, 4, 4, 8, true>); set(k4_cells<T, 4, 2, 8, true>);
+    set(k4_cells<T, 2, 2, 4, true>); set(k4_cells<T, 8, 4, 16, true>);
     return e;
 }
 
@@ -616,7 +628,7 @@ void enqueue_iteration(Impl<T>& im, int ncases, cudaStream_t s, cudaEvent_t* ev 
             case 1: k2_face_params<T><<<sp.total, 128, 0, s>>>(b); break;
             case 2: k3_macro<T><<<sp.total, K3_THREADS, 0, s>>>(b); break;
             case 3: k_tables<T><<<sp.total, 128, 0, s>>>(b); break;
-            case 4: launch_k4<T>(sp.shape, sp.total, sp.smem, b, s); break;
+            case 4: launch_k4<T>(im.any_implicit, sp.shape, sp.total, sp.smem, b, s); break;
         }
     }
     if (ev) {
@@ -719,7 +731,7 @@ hbugks_status autotune(hbugks_t h, Impl<T>& im, int ncases)
         std::lock_guard<std::mutex> lk(tune_cache().mu);
         for (int k = 0; k < ncases; ++k) {
             const HostCase& hc = im.hc[k];
-            keys[k] = {hc.nx, hc.ny, hc.nu, hc.nv, hc.nvb, hc.nt, (int)sizeof(T), sms};
+            keys[k] = {hc.nx, hc.ny, hc.nu, hc.nv, hc.nvb, hc.nt, (int)sizeof(T), sms, hc.src.phys.spectral_implicit};
             auto it = tune_cache().best.find(keys[k]);
             if (it != tune_cache().best.end()) im.hc[k].k4shape = it->second;
             else need = true;
@@ -748,9 +760,10 @@ hbugks_status autotune(hbugks_t h, Impl<T>& im, int ncases)
                 const int off[2] = {0, ((hc.nx + S.tx - 1) / S.tx) * ((hc.ny + S.ty - 1) / S.ty) * hc.nvb};
                 HB_CK(cudaMemcpyAsync(im.d_tune_off, off, sizeof off, cudaMemcpyHostToDevice, h->s));
                 const Batch<T> b{im.d_cases + k, 1, im.d_tune_off};
-                launch_k4<T>(sh, off[1], smem, b, h->s);
+                const bool imp = hc.src.phys.spectral_implicit != 0;
+                launch_k4<T>(imp, sh, off[1], smem, b, h->s);
                 HB_CK(cudaEventRecord(e0, h->s));
-                for (int r = 0; r < 3; ++r) launch_k4<T>(sh, off[1], smem, b, h->s);
+                for (int r = 0; r < 3; ++r) launch_k4<T>(imp, sh, off[1], smem, b, h->s);
                 HB_CK(cudaEventRecord(e1, h->s));
                 HB_CK(cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -773,8 +786,10 @@ template <typename T>
 hbugks_status do_create(hbugks_t h, Impl<T>& im, int ncases, const hbugks_case* cases)
 {
     plan(im, ncases, cases, h->ws);
-    for (auto& hc : im.hc)
+    for (auto& hc : im.hc) {
         if (hc.k4shape < 0) return HBUGKS_EINVAL;
+        if (hc.src.phys.spectral_implicit) im.any_implicit = true;
+    }
     HB_CK(set_smem_attributes<T>());
     std::vector<std::vector<char>> keep;
     for (int k = 0; k < ncases; ++k) HB_CK(upload_case(im.hc[k], im.dc[k], h->s, keep));

@@ -347,10 +347,12 @@ struct K4Layout {
 // every tile cell and the upwind halo cells and evaluates the flux through each one's downwind face (every
 // face of the tile exactly once); the second pass applies Eq. fv_h to the tile cells.  The second pass of
 // level n runs together with the first pass of level n + 1 (fluxes double buffered), so one barrier separates
-// the levels.  Batch k of bulk copies (the halo rectangle and face parameters of level k, the cell
+// the levels.  With IMP and a case that asks for it, the spectral source is taken at the new iterate: pass 2
+// leaves each level's right-hand side in the own-cell store and a last pass applies the per-cell inverse
+// across levels.  Batch k of bulk copies (the halo rectangle and face parameters of level k, the cell
 // coefficients of level k - 1; batch 0 also every level of the tile's own cells) completes on mbarrier k & 1
 // and is issued one level ahead of its use.
-template <typename T, int TX, int TY, int NW>
+template <typename T, int TX, int TY, int NW, bool IMP>
 __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
 {
     using L = K4Layout<T, TX, TY>;
@@ -476,7 +478,7 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
     const int qoffy = yneg ? F_QR : F_QL, loffy = yneg ? F_LBR : F_LBL;
     int* err = cd.err;
 
-    const bool implicit = cd.spectral_implicit != 0;
+    const bool implicit = IMP && cd.spectral_implicit != 0;   // IMP = false compiles the explicit form alone
     // a tile none of whose cells touches a wall: every stencil neighbour exists
     const bool interior = i0 >= 1 && j0 >= 1 && i0 + TX <= nx - 1 && j0 + TY <= ny - 1;
     constexpr bool PAIRED = NCT == 2 * NW;                    // each warp owns two tile cells in pass 1
