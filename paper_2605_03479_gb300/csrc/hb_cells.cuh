@@ -219,14 +219,21 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
         const T* cb = buf + (size_t)(k % S) * G * 2 * blk;
         const int vb0 = k * G, gk = min(G, nvb - vb0);
         if (valid) {
+            // the velocities of block g + 1 are loaded while block g is summed
+            int ncls = __ldg(vcls + vb0);
+            T nu_ = __ldg(tu + vb0 * VB + lane), nv_ = __ldg(tv + vb0 * VB + lane), nw_ = __ldg(tw + vb0 * VB + lane);
             for (int g = 0; g < gk; ++g) {
-                const int cls = __ldg(vcls + vb0 + g);
+                const int cls = ncls;
+                const T u = nu_, v = nv_, w = nw_;
+                if (g + 1 < gk) {
+                    const int a1 = (vb0 + g + 1) * VB + lane;
+                    ncls = __ldg(vcls + vb0 + g + 1);
+                    nu_ = __ldg(tu + a1); nv_ = __ldg(tv + a1); nw_ = __ldg(tw + a1);
+                }
                 if (cls != cur) {
                     if (cur >= 0) flush();
                     cur = cls;
                 }
-                const int a = (vb0 + g) * VB + lane;
-                const T u = __ldg(tu + a), v = __ldg(tv + a), w = __ldg(tw + a);
                 const T* ph = cb + (size_t)(2 * g) * blk + (size_t)kc * VB + lane;
                 const T* pb = ph + blk;
                 const T f0 = ph[0], g0 = pb[0];
