@@ -109,6 +109,29 @@ def tanh_nodes(n: int, ratio: float) -> np.ndarray:
     return x
 
 
+def wall_refined_nodes(n: int, ds_min: float, length: float = 1.0) -> np.ndarray:
+    """Nodes on [0, length] of the same tanh family, refined toward both walls so that the two wall cells are
+    ds_min wide (the paper's cavity meshes, Sec 3.1.1: 90 rows, 0.001 H at every wall).  beta by bisection:
+    the wall cell width length/2 (1 - tanh(beta (1 - 2/n)) / tanh(beta)) falls monotonically with beta."""
+    if not (0.0 < ds_min < length / n):
+        raise ValueError("ds_min must lie below the uniform spacing")
+    j = np.arange(n + 1)
+
+    def nodes(beta):
+        return 0.5 * length * (1.0 + np.tanh(beta * (2.0 * j / n - 1.0)) / math.tanh(beta))
+
+    lo, hi = 1e-6, 40.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if nodes(mid)[1] > ds_min:
+            lo = mid
+        else:
+            hi = mid
+    x = nodes(0.5 * (lo + hi))
+    x[0], x[-1] = 0.0, length
+    return x
+
+
 # ------------------------------------------------------------------- velocity grids
 
 def midpoint_grid(n: int, half_width: float = 4.0):
@@ -118,32 +141,58 @@ def midpoint_grid(n: int, half_width: float = 4.0):
     return x, np.full(n, h)
 
 
+def gauss_hermite_grid(n: int):
+    """n-point Gauss-Hermite rule as a discrete-velocity grid: the nodes of the weight e^{-u^2} (the rest
+    Maxwellian's shape in these units) and the weights w_j e^{u_j^2}, so that sum_j W_j f(u_j) approximates
+    the plain integral of f.  Exact for f = polynomial x e^{-u^2} up to degree 2n - 1.  The nodes reach past
+    +-4 (6.59 for n = 28)."""
+    x, w = np.polynomial.hermite.hermgauss(n)
+    return x, w * np.exp(x * x)
+
+
 # ------------------------------------------------------------------- case builders
 
 def make_case(name: str, ncell: int, nvel: int, *, kn: float, st: float, nh: int, pr: float = 1.0,
               stretched_ratio: float | None = None, drive: str = "shear", amp: float = 0.01,
               precision: int = 0, cfl: float = 0.8, half_width: float = 4.0, ncell_y: int | None = None,
-              nvel_y: int | None = None) -> Case:
-    """A cavity [0,1]^2 with ncell x ncell cells and an nvel x nvel midpoint velocity grid on [-L, L]^2.
+              nvel_y: int | None = None, aspect: float = 1.0, ds_min: float | None = None,
+              vgrid: str = "midpoint", lid_mean: float = 0.0) -> Case:
+    """A cavity [0,A] x [0,1] (A = aspect) with ncell x ncell_y cells and an nvel x nvel_y velocity grid.
 
-    drive = "shear": top lid U_w = amp cos(omega t) (Eq. lid_velocity with zero mean), all walls at T0.
+    Mesh: uniform; tanh-stretched to an adjacent-cell ratio (stretched_ratio); or refined toward every wall to
+    a wall cell of ds_min (the same ds_min on both axes).  Velocity grid: the midpoint rule on [-L, L]
+    (vgrid "midpoint") or the Gauss-Hermite rule (vgrid "gauss_hermite"; its largest node bounds the speeds).
+    drive = "shear": top lid U_w = lid_mean + amp cos(omega t) (Eq. lid_velocity), all walls at T0.
     drive = "thermal": bottom wall T_w = T0 (1 + amp sin(omega t)), all walls at rest.
+    drive = "thermal_top": top wall T_w = T0 (1 + amp cos(omega t)), all walls at rest (Sec 3.2).
     drive = "rest": every wall at rest and at T0."""
     ny = ncell if ncell_y is None else ncell_y
-    if stretched_ratio:
-        xn, yn = tanh_nodes(ncell, stretched_ratio), tanh_nodes(ny, stretched_ratio)
+    if ds_min is not None:
+        xn, yn = wall_refined_nodes(ncell, ds_min, aspect), wall_refined_nodes(ny, ds_min)
+    elif stretched_ratio:
+        xn, yn = aspect * tanh_nodes(ncell, stretched_ratio), tanh_nodes(ny, stretched_ratio)
     else:
-        xn, yn = uniform_nodes(ncell), uniform_nodes(ny)
-    u, wu = midpoint_grid(nvel, half_width)
-    v, wv = midpoint_grid(nvel if nvel_y is None else nvel_y, half_width)
+        xn, yn = uniform_nodes(ncell, aspect), uniform_nodes(ny)
+    nvy = nvel if nvel_y is None else nvel_y
+    if vgrid == "midpoint":
+        (u, wu), (v, wv) = midpoint_grid(nvel, half_width), midpoint_grid(nvy, half_width)
+        umax = vmax = half_width
+    elif vgrid == "gauss_hermite":
+        (u, wu), (v, wv) = gauss_hermite_grid(nvel), gauss_hermite_grid(nvy)
+        umax, vmax = float(np.max(np.abs(u))), float(np.max(np.abs(v)))
+    else:
+        raise ValueError(vgrid)
     walls = [rest_wall() for _ in range(4)]
     if drive == "shear":
+        walls[TOP][0] = lid_mean
         walls[TOP][3] = amp                   # U_re: amp cos(theta)
     elif drive == "thermal":
         walls[BOTTOM][8] = -amp               # T_im = -amp: Re(-i amp e^{i theta}) = amp sin(theta)
+    elif drive == "thermal_top":
+        walls[TOP][7] = amp                   # T_re = amp: amp cos(theta)
     elif drive != "rest":
         raise ValueError(drive)
-    return Case(name=name, xnodes=xn, ynodes=yn, u=u, wu=wu, v=v, wv=wv, umax=half_width, vmax=half_width,
+    return Case(name=name, xnodes=xn, ynodes=yn, u=u, wu=wu, v=v, wv=wv, umax=umax, vmax=vmax,
                 kn=kn, st=st, n_harmonics=nh, pr=pr, cfl=cfl, precision=precision, walls=walls)
 
 
@@ -194,6 +243,48 @@ def config5(precision: int = 1) -> Case:
     Kn 0.05, St 5, N_H 5 (N_T = 11)."""
     return make_case("thermal128_v64_nh5", 128, 64, kn=0.05, st=5.0, nh=5, pr=2.0 / 3.0, drive="thermal",
                      amp=0.5, precision=precision)
+
+
+# ----------------------------------------------------- the paper's own cavity workloads (Sec 3)
+
+PAPER_ROWS = 90            # cells across the cavity height (Sec 3.1.1)
+PAPER_DS_MIN = 0.001       # wall cell width in cavity heights (Sec 3.1.1)
+
+
+def kn_from_reynolds(re: float, u_mean: float, w_vss: float = 0.81, alpha_vss: float = 1.0) -> float:
+    """The Knudsen number whose reference viscosity (Eq. def_Kn) is mu(T0) = rho0 U_mean H / Re
+    (Eq. def_Re_mu0), with rho0 = H = 1 and sqrt(2 R T0) = 1, so that the cases of the continuum limit
+    (Sec 3.3) pass through the same Kn input as every other case."""
+    c_vss = 4.0 * alpha_vss * (5.0 - 2.0 * w_vss) * (7.0 - 2.0 * w_vss) / (5.0 * (alpha_vss + 1.0) * (alpha_vss + 2.0))
+    return c_vss * (u_mean / re) / math.sqrt(math.pi)
+
+
+def paper_shear_case(kn: float, st: float, aspect: float = 1.0, *, nh: int = 1, amp: float = 0.0015,
+                     precision: int = 0, rows: int = PAPER_ROWS, ds_min: float = PAPER_DS_MIN) -> Case:
+    """Shear-driven cavity of Sec 3.1: aspect A = L/H with round(A rows) x rows cells refined to ds_min at
+    every wall, lid 0.0015 cos(omega t), Shakhov Pr 2/3; 28 x 28 Gauss-Hermite velocities for Kn <= 0.1,
+    the 64 x 64 midpoint rule on [-4, 4] otherwise."""
+    gh = kn <= 0.1
+    ncell = int(round(aspect * rows))
+    return make_case(f"paper_shear_A{aspect:g}_kn{kn:g}_st{st:g}", ncell, 28 if gh else 64, kn=kn, st=st, nh=nh,
+                     pr=2.0 / 3.0, drive="shear", amp=amp, precision=precision, ncell_y=rows, aspect=aspect,
+                     ds_min=ds_min, vgrid="gauss_hermite" if gh else "midpoint")
+
+
+def paper_thermal_case(kn: float, st: float = 2.0, *, nh: int = 2, amp: float = 0.3, precision: int = 0,
+                       rows: int = PAPER_ROWS, ds_min: float = PAPER_DS_MIN) -> Case:
+    """Thermally driven square cavity of Sec 3.2: the shear case's mesh, top wall T0 (1 + 0.3 cos(omega t)),
+    N_H = 2, Shakhov Pr 2/3, one velocity grid for every Kn (the 64 x 64 midpoint rule on [-4, 4])."""
+    return make_case(f"paper_thermal_kn{kn:g}_st{st:g}_nh{nh}", rows, 64, kn=kn, st=st, nh=nh, pr=2.0 / 3.0,
+                     drive="thermal_top", amp=amp, precision=precision, ds_min=ds_min)
+
+
+def continuum_case(re: float, *, u_mean: float = 0.15, amp: float = 0.0015, st: float = 1.0, precision: int = 0,
+                   rows: int = PAPER_ROWS, ds_min: float = PAPER_DS_MIN) -> Case:
+    """Continuum limit of Sec 3.3: lid U_w = 0.15 + 0.0015 cos(omega t), viscosity from Re (Eq. def_Re_mu0),
+    16 x 16 uniform velocities on [-4, 4], N_H = 1, Shakhov Pr 2/3."""
+    return make_case(f"continuum_re{re:g}", rows, 16, kn=kn_from_reynolds(re, u_mean), st=st, nh=1,
+                     pr=2.0 / 3.0, drive="shear", amp=amp, lid_mean=u_mean, precision=precision, ds_min=ds_min)
 
 
 # ------------------------------------------------------------------- initial states

@@ -6,7 +6,8 @@ Tolerances (written here, derived in the design doc):
   * FP32-split path: h, b, W within 2e-5 of the change plus 2e-7 of the magnitude after a few iterations;
     macroscopic fields per harmonic within 1e-5 relative at convergence (test_gpu_convergence.py).
 Edge cases: ragged tiles, a single cell, a one-cell column or row, N_H = 0 and the largest N_H = 7, odd
-velocity grids with zero nodes, the harmonic-mean face step.
+velocity grids with zero nodes, the harmonic-mean face step; and the paper's own workload ingredients:
+Gauss-Hermite grids, wall-refined meshes, aspect ratios 0.5 and 2, a lid with a mean velocity.
 """
 import numpy as np
 import pytest
@@ -71,13 +72,28 @@ CASES_FP64 = [
 ]
 
 
+# the paper's own workload ingredients (Sec 3): Gauss-Hermite velocities with nodes past +-4, wall-refined
+# meshes, aspect ratios 0.5 and 2, a lid with a mean velocity (continuum limit), the heated top wall
+CASES_PAPER = [
+    ("paper_gauss_hermite_aspect_half", lambda: I.make_case("p", 5, 12, kn=0.1, st=3.0, nh=1, pr=2 / 3,
+                                                            drive="shear", amp=0.02, ncell_y=9, aspect=0.5,
+                                                            ds_min=0.01, vgrid="gauss_hermite"), 6),
+    ("paper_continuum_lid_aspect_two", lambda: I.make_case("q", 10, 16, kn=I.kn_from_reynolds(100.0, 0.15),
+                                                           st=1.0, nh=1, pr=2 / 3, drive="shear", amp=0.0015,
+                                                           lid_mean=0.15, ncell_y=5, aspect=2.0, ds_min=0.02), 6),
+    ("paper_thermal_top_gauss_hermite", lambda: I.make_case("r", 6, 14, kn=0.05, st=2.0, nh=2, pr=2 / 3,
+                                                            drive="thermal_top", amp=0.3, ds_min=0.02,
+                                                            vgrid="gauss_hermite"), 5),
+]
+
+
 def _with(case, **kw):
     for k, v in kw.items():
         setattr(case, k, v)
     return case
 
 
-@pytest.mark.parametrize("name,factory,niter", CASES_FP64, ids=[c[0] for c in CASES_FP64])
+@pytest.mark.parametrize("name,factory,niter", CASES_FP64 + CASES_PAPER, ids=[c[0] for c in CASES_FP64 + CASES_PAPER])
 def test_fp64_matches_oracle(hb, name, factory, niter):
     case = factory()
     init, g, o, res_g, res_o = run_both(hb, case, niter)
@@ -94,7 +110,8 @@ def test_fp64_config1_size_matches_oracle(hb):
         close(g[k], o[k], init[k], 1e-10, 1e-13)
 
 
-@pytest.mark.parametrize("name,factory,niter", CASES_FP64[:4], ids=[c[0] for c in CASES_FP64[:4]])
+@pytest.mark.parametrize("name,factory,niter", CASES_FP64[:4] + CASES_PAPER,
+                         ids=[c[0] for c in CASES_FP64[:4] + CASES_PAPER])
 def test_fp32_split_matches_oracle(hb, name, factory, niter):
     case = factory()
     case.precision = 1
