@@ -43,6 +43,13 @@ def workloads():
         "shear32_v24_nh1_fp64": lambda: [I.config1()],
         "shear64tanh_v32_nh1_sweep12_fp64": lambda: I.config2_cases(),
         "batch48_fp32split": lambda: I.config4_cases(precision=1),
+        # the paper's shear cavities (Sec 3.1.1): aspect 0.5, 1, 2 on 90-row wall-refined meshes, 28 x 28
+        # Gauss-Hermite velocities, Kn 0.1, St 30, N_H 1, in one handle
+        "paper_shear_A0.5_1_2_gh28_st30_fp32split":
+            lambda: [I.paper_shear_case(0.1, 30.0, a, precision=1) for a in (0.5, 1.0, 2.0)],
+        "paper_shear_A0.5_1_2_gh28_st30_fp64":
+            lambda: [I.paper_shear_case(0.1, 30.0, a, precision=0) for a in (0.5, 1.0, 2.0)],
+        "paper_thermal90_v64_nh2_fp32split": lambda: [I.paper_thermal_case(0.1, 2.0, precision=1)],
     }
 
 
@@ -417,10 +424,12 @@ def main():
     if names[top] in alg:
         ach = alg[names[top]] * upd / (kms[top] * 1e-3) / 1e9
         # DRAM bytes per update of the micro update (dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-        # launch of k4_cells<float, 4, 4, 8> on the 64x64 / 48x48 / N_T 7 thermal cavity), scaled by updates
+        # launch of k4_cells<float, 4, 4, 8> on the 64x64 / 48x48 / N_T 7 thermal cavity), scaled by updates;
+        # only where the launches match that capture: 4x4 tiles, velocity sign classes with no padded slots
         traffic = None
         if names[top] == "micro_update" and case.precision == 1 and all(
-                s.tile_shape(k) == (4, 4) for k in range(len(cases))):
+                s.tile_shape(k) == (4, 4) and c.nu % 2 == 0 and c.nv % 2 == 0
+                and (c.nu // 2) * (c.nv // 2) % 32 == 0 for k, c in enumerate(cases)):
             traffic = 17.55 * upd
         roof = {"kernel": names[top], "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_source": peak_kind, "traffic": traffic,
