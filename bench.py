@@ -370,7 +370,8 @@ def main():
         line = {"metric": METRIC, "value": ups, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
                 "warmup": W_, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-                "config": {"workload": args.workload + " (oracle sample)", "sample": sample},
+                "config": describe(args.workload, cases, sum(c.updates_per_iteration() for c in cases), world),
+                "sample": sample,
                 "cpu_baseline": {"value": ups, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
                 "e2e": {"value": ups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
