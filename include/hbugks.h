@@ -47,7 +47,7 @@ typedef enum {
     HBUGKS_NOT_CONVERGED = 1,   /* warning: the iteration budget ran out before the residual target */
     HBUGKS_EINVAL = -1,         /* invalid argument (sizes, pointers, unsupported combination) */
     HBUGKS_ECUDA = -2,          /* a CUDA runtime call failed */
-    HBUGKS_ENOMEM = -3,         /* workspace smaller than hbugks_workspace_bytes() */
+    HBUGKS_ENOMEM = -3,         /* workspace smaller than hbugks_workspace_bytes(), or host memory exhausted */
     HBUGKS_DIVERGED = -4,       /* a residual became NaN/Inf or exceeded 1e10 */
     HBUGKS_TIMEOUT = -5         /* reserved for bounded device-side waits */
 } hbugks_status;
@@ -116,7 +116,10 @@ typedef struct {
 } hbugks_case;
 
 /* Device workspace (bytes) a handle for these cases needs; 0 if the cases are invalid.
- * All cases of one handle must have the same precision. */
+ * All cases of one handle must have the same precision.  Invalid: a non-finite or non-positive size, weight,
+ * Kn, CFL, gamma, Pr, VSS alpha or speed bound; non-finite nodes or wall parameters; nodes not increasing; a
+ * wall temperature <= 0 on some level; N_T > 15; or a case so large that its per-face or per-cell expm1
+ * tables ((nf or 2 nc) x N_T x (nu + nv) elements) exceed 2^31 - 1 elements, the kernels' 32-bit offsets. */
 HBUGKS_API size_t hbugks_workspace_bytes(int ncases, const hbugks_case* cases);
 
 /* Create a handle for `ncases` cases (a batch of one or more uneven cases iterated together).

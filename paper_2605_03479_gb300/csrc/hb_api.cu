@@ -2,6 +2,7 @@
 // capture of the pseudo-time iteration, state and field conversions.  All device memory lives in the
 // caller's workspace; the library allocates none.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -110,6 +111,9 @@ int pick_k4_shape(int nt)
     return -1;
 }
 
+// finite and strictly positive
+inline bool pos(double x) { return std::isfinite(x) && x > 0; }
+
 bool validate(const hbugks_case& c)
 {
     const hbugks_mesh& m = c.mesh;
@@ -118,18 +122,29 @@ bool validate(const hbugks_case& c)
     if (m.nx < 1 || m.ny < 1 || !m.xnodes || !m.ynodes) return false;
     if (g.nu < 1 || g.nv < 1 || !g.u || !g.v || !g.wu || !g.wv) return false;
     if (p.n_harmonics < 0 || 2 * p.n_harmonics + 1 > MAXNT) return false;
-    if (!(p.kn > 0) || !(p.cfl > 0) || !(p.st >= 0) || !(p.gamma > 0)) return false;
+    if (!pos(p.kn) || !pos(p.cfl) || !(std::isfinite(p.st) && p.st >= 0) || !pos(p.gamma)) return false;
+    if (!pos(p.pr) || !std::isfinite(p.w_vss) || !pos(p.alpha_vss) || !pos(g.umax) || !pos(g.vmax)) return false;
     if (p.precision != 0 && p.precision != 1) return false;
     if (p.face_step != 0 && p.face_step != 1) return false;
     if (p.td_steps < 0 || (p.td_steps > 0 && (p.n_harmonics != 0 || !(p.st > 0)))) return false;
     if (p.spectral_implicit != 0 && p.spectral_implicit != 1) return false;
-    for (int i = 0; i < m.nx; ++i) if (!(m.xnodes[i + 1] > m.xnodes[i])) return false;
-    for (int j = 0; j < m.ny; ++j) if (!(m.ynodes[j + 1] > m.ynodes[j])) return false;
-    for (int i = 0; i < g.nu; ++i) if (!(g.wu[i] > 0)) return false;
-    for (int j = 0; j < g.nv; ++j) if (!(g.wv[j] > 0)) return false;
+    // the kernels index the per-face and per-cell expm1 tables ([nf][nt][nu + nv], [nc][nt][2][nu + nv]) and a
+    // cell's 32-lane rows with 32-bit element offsets
+    {
+        const long long nc = (long long)m.nx * m.ny, nt = 2LL * p.n_harmonics + 1, nuv = (long long)g.nu + g.nv;
+        const long long nf = (long long)m.ny * (m.nx + 1) + (long long)(m.ny + 1) * m.nx;
+        if (nf * nt * nuv > INT_MAX || nc * nt * 2 * nuv > INT_MAX || nc * VB > INT_MAX) return false;
+    }
+    if (!std::isfinite(m.xnodes[0]) || !std::isfinite(m.ynodes[0])) return false;
+    for (int i = 0; i < m.nx; ++i) if (!(m.xnodes[i + 1] > m.xnodes[i]) || !std::isfinite(m.xnodes[i + 1])) return false;
+    for (int j = 0; j < m.ny; ++j) if (!(m.ynodes[j + 1] > m.ynodes[j]) || !std::isfinite(m.ynodes[j + 1])) return false;
+    for (int i = 0; i < g.nu; ++i) if (!pos(g.wu[i]) || !std::isfinite(g.u[i])) return false;
+    for (int j = 0; j < g.nv; ++j) if (!pos(g.wv[j]) || !std::isfinite(g.v[j])) return false;
     const int nslot = p.td_steps > 0 ? p.td_steps : 2 * p.n_harmonics + 1;
     for (int w = 0; w < 4; ++w) {
         const hbugks_wall& wl = c.walls[w];
+        const double vals[9] = {wl.u_mean, wl.v_mean, wl.T_mean, wl.u_re, wl.u_im, wl.v_re, wl.v_im, wl.T_re, wl.T_im};
+        for (double x : vals) if (!std::isfinite(x)) return false;
         for (int n = 0; n < nslot; ++n) {
             double th = p.td_steps > 0 ? 2.0 * M_PI * (n + 0.5) / nslot : 2.0 * M_PI * n / nslot;
             if (!(wl.T_mean + wl.T_re * cos(th) - wl.T_im * sin(th) > 0)) return false;
@@ -804,11 +819,25 @@ hbugks_status do_create(hbugks_t h, Impl<T>& im, int ncases, const hbugks_case* 
     return capture(h, im);
 }
 
+// runs fn on the handle's precision; a status-returning fn reports a C++ exception (host allocation) as a status,
+// so that none crosses the C ABI
 template <class F>
 auto dispatch(hbugks_t h, F&& fn) -> decltype(fn(*h->d))
 {
-    if (h->f) return fn(*h->f);
-    return fn(*h->d);
+    using R = decltype(fn(*h->d));
+    if constexpr (std::is_same<R, hbugks_status>::value) {
+        try {
+            if (h->f) return fn(*h->f);
+            return fn(*h->d);
+        } catch (const std::bad_alloc&) {
+            return HBUGKS_ENOMEM;
+        } catch (...) {
+            return HBUGKS_EINVAL;
+        }
+    } else {
+        if (h->f) return fn(*h->f);
+        return fn(*h->d);
+    }
 }
 
 }  // namespace
@@ -885,12 +914,16 @@ size_t hbugks_workspace_bytes(int ncases, const hbugks_case* cases)
     if (ncases < 1 || !cases) return 0;
     for (int k = 0; k < ncases; ++k)
         if (!validate(cases[k]) || cases[k].phys.precision != cases[0].phys.precision) return 0;
-    if (cases[0].phys.precision == 1) {
-        Impl<float> im;
+    try {
+        if (cases[0].phys.precision == 1) {
+            Impl<float> im;
+            return plan(im, ncases, cases, nullptr);
+        }
+        Impl<double> im;
         return plan(im, ncases, cases, nullptr);
+    } catch (...) {
+        return 0;
     }
-    Impl<double> im;
-    return plan(im, ncases, cases, nullptr);
 }
 
 hbugks_status hbugks_create(int ncases, const hbugks_case* cases, void* d_workspace, size_t bytes,
@@ -907,7 +940,6 @@ hbugks_status hbugks_create(int ncases, const hbugks_case* cases, void* d_worksp
     h->user = (cudaStream_t)cuda_stream;
     h->ws = (char*)d_workspace;
     h->bytes = bytes;
-    h->st_host.resize(ncases);
     hbugks_status rc = HBUGKS_OK;
     if (cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
@@ -916,12 +948,19 @@ hbugks_status hbugks_create(int ncases, const hbugks_case* cases, void* d_worksp
         return HBUGKS_ECUDA;
     }
     if ((rc = begin(h)) != HBUGKS_OK) { hbugks_destroy(h); return rc; }
-    if (h->precision == 1) {
-        h->f = new Impl<float>;
-        rc = do_create(h, *h->f, ncases, cases);
-    } else {
-        h->d = new Impl<double>;
-        rc = do_create(h, *h->d, ncases, cases);
+    try {
+        h->st_host.resize(ncases);
+        if (h->precision == 1) {
+            h->f = new Impl<float>;
+            rc = do_create(h, *h->f, ncases, cases);
+        } else {
+            h->d = new Impl<double>;
+            rc = do_create(h, *h->d, ncases, cases);
+        }
+    } catch (const std::bad_alloc&) {
+        rc = HBUGKS_ENOMEM;
+    } catch (...) {
+        rc = HBUGKS_EINVAL;
     }
     if (rc == HBUGKS_OK) rc = end(h);
     if (rc != HBUGKS_OK) { hbugks_destroy(h); return rc; }
@@ -1288,7 +1327,7 @@ const char* hbugks_status_string(hbugks_status s)
         case HBUGKS_NOT_CONVERGED: return "not converged";
         case HBUGKS_EINVAL: return "invalid argument";
         case HBUGKS_ECUDA: return "CUDA error";
-        case HBUGKS_ENOMEM: return "workspace too small";
+        case HBUGKS_ENOMEM: return "workspace too small or host memory exhausted";
         case HBUGKS_DIVERGED: return "diverged";
         case HBUGKS_TIMEOUT: return "device wait timed out";
     }

@@ -74,3 +74,31 @@ def test_time_domain_mode_needs_one_level_and_a_frequency():
     assert hb.workspace_bytes([c]) == 0
     c.st, c.td_steps = 1.0, -1
     assert hb.workspace_bytes([c]) == 0
+
+
+@pytest.mark.parametrize("spoil", [
+    lambda c: c.u.__setitem__(3, np.nan),                  # a velocity node
+    lambda c: c.wv.__setitem__(0, np.inf),                 # a weight
+    lambda c: c.xnodes.__setitem__(-1, np.inf),            # the last mesh node
+    lambda c: setattr(c, "kn", np.inf),
+    lambda c: setattr(c, "st", np.nan),
+    lambda c: setattr(c, "cfl", np.inf),
+    lambda c: setattr(c, "pr", 0.0),
+    lambda c: setattr(c, "umax", 0.0),
+    lambda c: c.walls[2].__setitem__(3, np.nan),           # the lid amplitude
+], ids=["nan_node", "inf_weight", "inf_mesh_node", "inf_kn", "nan_st", "inf_cfl", "zero_pr", "zero_umax",
+        "nan_wall"])
+def test_non_finite_inputs_are_rejected(L, spoil):
+    c = I.config1()
+    assert hbugks.workspace_bytes([c]) > 0
+    spoil(c)
+    assert hbugks.workspace_bytes([c]) == 0
+
+
+def test_cases_beyond_32_bit_table_offsets_are_rejected(L):
+    # 3000 x 3000 cells, 16 x 16 velocities, N_T = 15: the per-cell expm1 table [nc][nt][2][nu + nv] would hold
+    # 8.6e9 elements (its state, 552 GB, would not fit in HBM either); 1000 x 1000 cells keep it at 9.6e8
+    big = I.make_case("big", 3000, 16, kn=0.1, st=1.0, nh=7, drive="shear")
+    assert hbugks.workspace_bytes([big]) == 0
+    ok = I.make_case("ok", 1000, 16, kn=0.1, st=1.0, nh=7, drive="shear")
+    assert hbugks.workspace_bytes([ok]) > 0
