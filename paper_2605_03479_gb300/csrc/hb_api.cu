@@ -37,6 +37,25 @@ cudaError_t& last_cuda_error()
 
 constexpr int CHUNK = 16;   // iterations per captured graph
 
+// timing events destroyed on every return path
+struct Events {
+    std::vector<cudaEvent_t> ev;
+    cudaError_t create(int n)
+    {
+        ev.assign(n, nullptr);
+        for (auto& e : ev) {
+            const cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) { e = nullptr; return r; }
+        }
+        return cudaSuccess;
+    }
+    ~Events()
+    {
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
 // bump allocator over the workspace; with base == nullptr it only measures
 struct Carver {
     char* base;
@@ -756,9 +775,9 @@ hbugks_status autotune(hbugks_t h, Impl<T>& im, int ncases)
         k_begin_call<<<(ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, ncases);
         enqueue_iteration(im, ncases, h->s);
         k_begin_call<<<(ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, ncases);
-        cudaEvent_t e0, e1;
-        HB_CK(cudaEventCreate(&e0));
-        HB_CK(cudaEventCreate(&e1));
+        Events evs;
+        HB_CK(evs.create(2));
+        const cudaEvent_t e0 = evs.ev[0], e1 = evs.ev[1];
         for (int k = 0; k < ncases; ++k) {
             {
                 std::lock_guard<std::mutex> lk(tune_cache().mu);
@@ -789,8 +808,6 @@ hbugks_status autotune(hbugks_t h, Impl<T>& im, int ncases)
             std::lock_guard<std::mutex> lk(tune_cache().mu);
             tune_cache().best[keys[k]] = best;
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         HB_CK(cudaGetLastError());
     }
     for (auto& hc : im.hc) set_k4_blocks(hc);
@@ -1235,8 +1252,9 @@ hbugks_status hbugks_profile_kernels(hbugks_t h, int n, double* ms)
     return dispatch(h, [&](auto& im) -> hbugks_status {
         hbugks_status rc = begin(h);
         if (rc) return rc;
-        cudaEvent_t ev[10];
-        for (int k = 0; k < 10; ++k) HB_CK(cudaEventCreate(&ev[k]));
+        Events evs;
+        HB_CK(evs.create(10));
+        cudaEvent_t* ev = evs.ev.data();
         HB_CK(cudaMemsetAsync(im.d_tol, 0, sizeof(double), h->s));
         k_begin_call<<<(h->ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, h->ncases);
         double acc[5] = {0, 0, 0, 0, 0};
@@ -1249,7 +1267,6 @@ hbugks_status hbugks_profile_kernels(hbugks_t h, int n, double* ms)
                 acc[k] += t;
             }
         }
-        for (int k = 0; k < 10; ++k) cudaEventDestroy(ev[k]);
         for (int k = 0; k < 5; ++k) ms[k] = acc[k] / n;
         return end(h);
     });
