@@ -20,7 +20,7 @@
  * Units: lengths in cavity heights H, velocities in sqrt(2 R T0) (so R T0 = 1/2), temperatures in T0.
  * lambda = 1/(2RT); lam_ref = lambda(T0) (= 1 in these units).  D = 2, K = 1 (Sec 2.1).
  *
- * Readings of points the paper leaves open (each one is listed in the design doc):
+ * Readings of points the paper leaves open (the CUDA path takes the same ones):
  *   - reduced Shakhov terms H+, B+ : g+ of Eq. shakhov integrated over the internal variable xi;
  *   - heat flux for the Shakhov term of the cell update taken from h^k (q^k);
  *   - limiter = van Leer on non-uniform spacing; one-sided difference in wall-adjacent cells;
