@@ -30,7 +30,10 @@
  *   - C1..C5 by their Taylor series in x = dG/tau for x < 1, by the printed forms otherwise;
  *   - one dG per cell (max over levels of nu_conv), u_max = truncation bound of the velocity grid;
  *   - wall: incident part from the interior reconstruction through the same integral solution, with
- *     the wall-side equilibrium taken from the mixed (incident + free-transport-reflected) distribution;
+ *     the wall-side equilibrium taken from the mixed (incident + free-transport-reflected) distribution
+ *     (pinned by zero wall mass flux, the rest fixed point, mirror and transpose symmetries and the
+ *     collisionless limits of the oscillating lid; the choice of that equilibrium itself has no closed form
+ *     to compare with);
  *   - velocity nodes with u_n == 0 at an interior face take the average of the two reconstructions.
  */
 #include <math.h>

@@ -369,3 +369,44 @@ def test_implicit_spectral_source_damps_the_modes_forward_euler_amplifies():
     _, _, ri = _run(c, 1, 600)
     assert not (re_[-1][0] < 1e-2)            # grown or NaN
     assert ri[-1][0] < 1e-9
+
+
+# ------------------------------------------------------------------ collisionless limit at high frequency (Sec 3.1.2)
+
+def _lid_amplitudes(st, iters):
+    """Lid-averaged first harmonics (Eqs. nondim_U, nondim_tau: cell-width weighted over the row under the lid)
+    of a 4 x 12 shear cavity refined to 0.001 H at the top and bottom walls, 16 x 16 Gauss-Hermite velocities,
+    Kn 0.1, lid 0.0015 cos(omega t), N_H 1, the spectral source at the new iterate (the explicit form grows at
+    St 30).  Returns U~ and tau~ relative to the lid's own first harmonic (U_a / 2 under Eq. dft_general), and
+    the complex ratios for their phases."""
+    c = I.make_case("lid", 4, 16, kn=0.1, st=st, nh=1, pr=2 / 3, drive="shear", amp=0.0015, ncell_y=12,
+                    vgrid="gauss_hermite")
+    c.ynodes = I.wall_refined_nodes(12, 0.001)
+    c.spectral_implicit = 1
+    P = O.Problem(c)
+    W, h, b = I.initial_state(c)
+    O.iterate(P, W, h, b, iters)
+    lv = np.stack([O.fields(P, h, b, n) for n in range(c.nt)])
+    H = O.harmonics(lv)                                    # (k, field, cell)
+    dx = np.diff(c.xnodes)
+    top = slice((c.ny - 1) * c.nx, c.ny * c.nx)
+    U1 = np.sum(H[1, 1, top] * dx) / c.xnodes[-1]
+    T1 = np.sum(H[1, 4, top] * dx) / c.xnodes[-1]
+    lid1 = 0.0015 / 2                                      # first harmonic of 0.0015 cos(omega t)
+    p0 = 0.5                                               # rho0 R T0
+    return abs(U1) / lid1, abs(T1) / (p0 * lid1), U1 / lid1, T1 / U1
+
+
+def test_collisionless_limits_of_the_oscillating_lid():
+    """Sec 3.1.2: at St 30 the forcing period is short against the collision time, so next to the diffuse lid the
+    molecules leaving it carry its velocity and those arriving carry none: U~ -> 1/2 and tau~ -> 1/sqrt(pi)
+    (p0 = 1/2, sqrt(2 R T0) = 1), the velocity in phase with the lid and the stress against it.  On this small
+    mesh they come within 1 % and 2 % (0.504 and 0.575); at St 0.5 the gas near the lid is not collisionless
+    and both miss by more than 10 % (0.589 and 0.491), so the check tells the regimes apart."""
+    Ut, tt, Uc, ratio = _lid_amplitudes(30.0, 400)
+    assert abs(Ut - 0.5) < 0.02 * 0.5, Ut
+    assert abs(tt - 1 / math.sqrt(math.pi)) < 0.02 / math.sqrt(math.pi), tt
+    assert abs(np.angle(Uc)) < 0.15, Uc                    # in phase with the lid (measured lag 0.07 rad)
+    assert abs(np.angle(-ratio)) < 0.15, ratio             # stress opposes the gas velocity
+    Ut, tt, _, _ = _lid_amplitudes(0.5, 800)
+    assert abs(Ut - 0.5) > 0.1 * 0.5 and abs(tt - 1 / math.sqrt(math.pi)) > 0.1 / math.sqrt(math.pi), (Ut, tt)
