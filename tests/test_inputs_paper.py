@@ -98,3 +98,23 @@ def test_mirror_symmetry_of_an_aspect_half_gauss_hermite_cavity():
     np.testing.assert_allclose(WB, Wm, rtol=0, atol=1e-13)
     np.testing.assert_allclose(hB, hm, rtol=0, atol=1e-13 * hA.max())
     np.testing.assert_allclose(bB, bm, rtol=0, atol=1e-13 * bA.max())
+
+
+def test_batch48_case_table_is_the_committed_one():
+    """The 48-case batch is drawn, not stored; the committed table (tests/golden/batch48_cases.txt, written by
+    tests/golden/write_batch48_cases.py) fixes the draw, so a change in numpy's PCG64 stream or in the draw
+    order shows here."""
+    import importlib.util
+    import os
+    gold = os.path.join(os.path.dirname(__file__), "golden")
+    spec = importlib.util.spec_from_file_location("write_batch48_cases", os.path.join(gold, "write_batch48_cases.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    with open(os.path.join(gold, "batch48_cases.txt")) as f:
+        committed = f.read().splitlines()
+    assert mod.table_lines() == committed
+    cases = I.config4_cases()
+    assert len(cases) == 48 and len({c.name for c in cases}) == 48
+    for c in cases:
+        assert 32 <= c.nx <= 96 and c.nx % 8 == 0 and c.nu in (24, 32, 40, 48) and 1 <= c.n_harmonics <= 3
+        assert 0.01 <= c.kn <= 10 and 0.1 <= c.st <= 10
