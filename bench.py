@@ -150,6 +150,22 @@ def run_oracle(case_full, steps, warmup, min_seconds=0.0):
     return ups, dt / n, sample
 
 
+def host_info() -> dict:
+    """The host the CPU baseline ran on: architecture, logical cores, CPU model where /proc/cpuinfo names one."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"machine": platform.machine(), "nproc": os.cpu_count(), "cpu": model}
+
+
 def slowest_rank_ms(ms: float, dist, device) -> float:
     """The job's step time: the maximum over ranks (every rank runs a replica; the job ends with the slowest)."""
     if dist is None:
@@ -372,7 +388,8 @@ def main():
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
                 "config": describe(args.workload, cases, sum(c.updates_per_iteration() for c in cases), world),
                 "sample": sample,
-                "cpu_baseline": {"value": ups, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                "cpu_baseline": {"value": ups, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                                 "host": host_info()},
                 "e2e": {"value": ups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -471,7 +488,7 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu:
         ups, sec, sample = run_oracle(case, 2, 0, min_seconds=10.0)
-        cpu = {"value": ups, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = {"value": ups, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "host": host_info()}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

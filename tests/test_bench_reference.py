@@ -31,6 +31,7 @@ def test_reference_line_matches_the_gpu_arm_contract():
     assert line["steps"] == 1 and line["warmup"] >= 3 and line["value"] > 0
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert cb["host"]["nproc"] >= 1 and cb["host"]["machine"]
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
 
