@@ -72,6 +72,16 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def smi_device(local: int) -> str:
+    """The nvidia-smi id (index or UUID) of the process's CUDA device `local`: CUDA_VISIBLE_DEVICES renumbers
+    the devices a process sees, nvidia-smi does not."""
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    items = [x.strip() for x in vis.split(",") if x.strip()]
+    if items and 0 <= local < len(items):
+        return items[local]
+    return str(local)
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -79,13 +89,13 @@ class Clocks:
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
-        self.idx = gpu_index
+        self.idx = smi_device(gpu_index)
         self.p = None
 
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-i", str(self.idx), "-lms", "100"], stdout=subprocess.PIPE,
+                                       "-i", self.idx, "-lms", "100"], stdout=subprocess.PIPE,
                                       stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None

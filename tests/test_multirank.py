@@ -45,3 +45,13 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.slowest_rank_ms(7.0, None, "cpu") == 7.0
     assert bench.job_updates_per_s(100, 1, 2.0) == pytest.approx(5e4)
+
+
+def test_clock_sampler_follows_cuda_visible_devices(monkeypatch):
+    import bench
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "3,5")
+    assert bench.smi_device(0) == "3" and bench.smi_device(1) == "5"
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "GPU-1a2b")
+    assert bench.smi_device(0) == "GPU-1a2b"
+    monkeypatch.delenv("CUDA_VISIBLE_DEVICES")
+    assert bench.smi_device(2) == "2"
