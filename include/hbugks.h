@@ -49,7 +49,8 @@ typedef enum {
     HBUGKS_ECUDA = -2,          /* a CUDA runtime call failed */
     HBUGKS_ENOMEM = -3,         /* workspace smaller than hbugks_workspace_bytes(), or host memory exhausted */
     HBUGKS_DIVERGED = -4,       /* a residual became NaN/Inf or exceeded 1e10 */
-    HBUGKS_TIMEOUT = -5         /* reserved for bounded device-side waits */
+    HBUGKS_TIMEOUT = -5         /* a bounded device-side wait ran out (500 ms for a bulk copy); the iteration
+                                   in which it happened left the state unchanged */
 } hbugks_status;
 
 /* Non-uniform Cartesian mesh of the cavity: node coordinates, nx + 1 and ny + 1 increasing values
@@ -178,7 +179,8 @@ HBUGKS_API const char* hbugks_status_string(hbugks_status s);
 HBUGKS_API const char* hbugks_cuda_error_string(void);
 
 /* Kernel-level timing support: enqueue `n` iterations on the handle's stream without any host
- * synchronisation or residual check (for timing with CUDA events around the call). */
+ * synchronisation or residual check (for timing with CUDA events around the call).  A device-side wait that
+ * runs out in these iterations is reported by the next hbugks_iterate call (HBUGKS_TIMEOUT). */
 HBUGKS_API hbugks_status hbugks_enqueue_iterations(hbugks_t h, int n);
 
 /* Kernel timing: run `n` iterations kernel by kernel (not graph-captured) with a CUDA event pair around each
@@ -196,8 +198,12 @@ HBUGKS_API hbugks_status hbugks_profile_kernels(hbugks_t h, int n, double* ms);
  * h, b[nt][nx*ny][nu*nv].  Its intermediate per-level fields live in a fixed array inside the library
  * (HBUGKS_NOALLOC_MAX_DOUBLES doubles, 4 MiB, held on every device that loads the library until the
  * process exits), so it requires 8 * nt * nx * ny <= HBUGKS_NOALLOC_MAX_DOUBLES and returns HBUGKS_EINVAL
- * otherwise.  It calls no allocating CUDA or library routine.  The first call on a device looks up that
- * device's address of the array; make that first call before any stream capture.  All calls share the
+ * otherwise.  It calls no allocating CUDA or library routine.  The first call on a device (and the first after
+ * the device's context has been rebuilt, for example by cudaDeviceReset) looks up that device's address of the
+ * array; make that first call before any stream capture.  The array is reserved when the library's device
+ * code is loaded into a context, which under CUDA's default lazy loading happens at the first call into the
+ * library on that device (this entry point, or hbugks_create): that first call must find about 4 MiB of
+ * device memory still free, and fails with HBUGKS_ECUDA otherwise.  All calls share the
  * one array, so calls whose work overlaps on the GPU (different streams, or different host threads) race and
  * must be serialised by the caller.  The paper has no counterpart of this entry point. */
 #define HBUGKS_NOALLOC_MAX_DOUBLES (1 << 19)
@@ -214,6 +220,16 @@ HBUGKS_API hbugks_status hbugks_harmonic_noalloc(int nx, int ny, int nu, int nv,
  * choice). */
 HBUGKS_API hbugks_status hbugks_get_tile_shape(hbugks_t h, int case_index, int* tx, int* ty);
 HBUGKS_API hbugks_status hbugks_set_tile_shape(hbugks_t h, int case_index, int tx, int ty);
+
+/* Failure-path test hook.  Every device-side wait of the iteration kernels (a bulk copy into shared memory
+ * completing on an mbarrier) is bounded by elapsed time: on expiry the kernel sets the handle's error word, its
+ * CTA waits (bounded) for the copies it has issued and exits, every later kernel of the iteration returns
+ * without work, and hbugks_iterate returns HBUGKS_TIMEOUT after the chunk of iterations in which it happened,
+ * with the state of the last completed iteration.  This call makes the micro-update kernel of the next
+ * iteration report its first wait as expired right after that wait has completed, so the whole failure path
+ * runs without any copy actually failing.  hbugks_iterate clears the hook together with the error word when it
+ * returns HBUGKS_TIMEOUT; the next call iterates normally.  The paper has no counterpart (failure handling). */
+HBUGKS_API hbugks_status hbugks_test_expire_wait(hbugks_t h);
 
 /* Number of kernel launches one iteration enqueues for this handle. */
 HBUGKS_API int hbugks_launches_per_iteration(hbugks_t h);

@@ -5,6 +5,7 @@ C++17 (no architecture-specific flags), so the same command builds on x86_64 and
 """
 from __future__ import annotations
 
+import glob
 import os
 import shutil
 import subprocess
@@ -13,8 +14,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = [os.path.join(HERE, "csrc", "hb_api.cu")]
-DEPS = [os.path.join(HERE, "csrc", f) for f in ("hb_common.cuh", "hb_kernels.cuh")] + \
-       [os.path.join(ROOT, "include", "hbugks.h")]
+# every header and source the library is compiled from: a change to any of them rebuilds it
+DEPS = sorted(glob.glob(os.path.join(HERE, "csrc", "*.cu*")) + glob.glob(os.path.join(ROOT, "include", "*.h")) +
+              [os.path.abspath(__file__)])
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libhbugks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -312,7 +312,7 @@ struct Impl {
     CaseDev<T>* d_cases = nullptr;
     CaseStatus* d_status = nullptr;
     double* d_tol = nullptr;
-    int* d_err = nullptr;
+    int* d_err = nullptr;            // [0] error word (a bounded wait expired), [1] test hook: expire the next wait
     int* d_off = nullptr;            // [table][ncases + 1]
     int* d_tune_off = nullptr;       // block offsets of a single-case launch (autotuning)
     std::vector<int> off_host;
@@ -364,7 +364,7 @@ size_t plan(Impl<T>& im, int ncases, const hbugks_case* cases, char* base)
     im.d_cases = cv.take<CaseDev<T>>(ncases);
     im.d_status = cv.take<CaseStatus>(ncases);
     im.d_tol = cv.take<double>(1);
-    im.d_err = cv.take<int>(1);
+    im.d_err = cv.take<int>(2);
     im.d_tune_off = cv.take<int>(2);
     // launch specs: K1 per shape, K2, K3, tables, K4 per shape; plus the step kernel (state setting only)
     im.specs.clear();
@@ -384,6 +384,7 @@ size_t plan(Impl<T>& im, int ncases, const hbugks_case* cases, char* base)
         im.dc[k].st = im.d_status + k;
         im.dc[k].tol = im.d_tol;
         im.dc[k].err = im.d_err;
+        im.dc[k].expire = im.d_err + 1;
     }
     fill_offsets(im, ncases);
     return cv.off + 256;
@@ -717,7 +718,7 @@ template <typename T>
 hbugks_status reset_rest(hbugks_t h, Impl<T>& im, int ncases)
 {
     HB_CK(cudaMemsetAsync(im.d_tol, 0, sizeof(double), h->s));
-    HB_CK(cudaMemsetAsync(im.d_err, 0, sizeof(int), h->s));
+    HB_CK(cudaMemsetAsync(im.d_err, 0, 2 * sizeof(int), h->s));
     k_status_reset<<<(ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, ncases, -1, 1);
     for (int k = 0; k < ncases; ++k) {
         const CaseDev<T>& d = im.dc[k];
@@ -905,19 +906,41 @@ __global__ void k_fields_canonical(int nc, int nu, int nv, int nt, const double*
     }
 }
 
-// device address of the scratch array, looked up once per device
+// the calling thread's current CUDA context, through the driver entry point the runtime hands out (the library
+// does not link the driver library itself); nullptr if it cannot be queried
+void* current_context()
+{
+    using Fn = int (*)(void**);
+    static Fn fn = []() -> Fn {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<Fn>(p);
+    }();
+    void* ctx = nullptr;
+    if (!fn || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
+
+// Device address of the scratch array, looked up once per device and context: the address belongs to the
+// context the module was loaded into, so after a context is torn down and rebuilt (cudaDeviceReset, a new
+// primary context) it is looked up again.
 double* noalloc_scratch(int dev)
 {
+    struct Entry { void* ctx; double* ptr; };
     static std::mutex mu;
-    static double* ptr[256] = {};
+    static Entry tab[256] = {};
     std::lock_guard<std::mutex> lock(mu);
     if (dev < 0 || dev >= 256) return nullptr;
-    if (!ptr[dev]) {
+    void* ctx = current_context();
+    if (!tab[dev].ptr || ctx == nullptr || ctx != tab[dev].ctx) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) return nullptr;
-        ptr[dev] = static_cast<double*>(p);
+        tab[dev] = Entry{ctx, static_cast<double*>(p)};
     }
-    return ptr[dev];
+    return tab[dev].ptr;
 }
 
 }  // namespace
@@ -1141,25 +1164,34 @@ hbugks_status hbugks_iterate(hbugks_t h, int max_iters, double tol_rho, int* ite
         k_begin_call<<<(h->ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, h->ncases);
         int done = 0;
         std::vector<CaseStatus>& st = h->st_host;
+        // statuses and the error word after every chunk of iterations: a wait that ran out ends the call at once
+        // (the kernels of later iterations return without work while the word is set)
+        auto poll = [&](int& err) -> hbugks_status {
+            HB_CK(cudaMemcpyAsync(st.data(), im.d_status, sizeof(CaseStatus) * h->ncases, cudaMemcpyDeviceToHost, h->s));
+            HB_CK(cudaMemcpyAsync(&err, im.d_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+            HB_CK(cudaStreamSynchronize(h->s));
+            return HBUGKS_OK;
+        };
+        int err = 0;
         while (done < max_iters) {
             int n = std::min(CHUNK, max_iters - done);
             if ((rc = launch_iters(h, n))) return rc;
             done += n;
-            HB_CK(cudaMemcpyAsync(st.data(), im.d_status, sizeof(CaseStatus) * h->ncases, cudaMemcpyDeviceToHost, h->s));
-            HB_CK(cudaStreamSynchronize(h->s));
+            if ((rc = poll(err))) return rc;
+            if (err) break;
             bool any = false;
             for (int k = 0; k < h->ncases; ++k) any = any || st[k].active;
             if (!any) break;
         }
-        if (done == 0) {
-            HB_CK(cudaMemcpyAsync(st.data(), im.d_status, sizeof(CaseStatus) * h->ncases, cudaMemcpyDeviceToHost, h->s));
-            HB_CK(cudaStreamSynchronize(h->s));
-        }
-        int err = 0;
-        HB_CK(cudaMemcpyAsync(&err, im.d_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
-        HB_CK(cudaStreamSynchronize(h->s));
+        if (done == 0 && (rc = poll(err))) return rc;
         if (err) {
-            HB_CK(cudaMemsetAsync(im.d_err, 0, sizeof(int), h->s));
+            // the state is the one before the failed iteration (its residual kernel did not run, so the state
+            // buffers did not swap); clear the error word and the test hook, and recompute the local steps of
+            // that state (the macro update had already replaced them with those of the abandoned iterate), so
+            // that the next call iterates normally
+            HB_CK(cudaMemsetAsync(im.d_err, 0, 2 * sizeof(int), h->s));
+            enqueue_steps(im, h->ncases, h->s);
+            HB_CK(cudaStreamSynchronize(h->s));
             end(h);
             return HBUGKS_TIMEOUT;
         }
@@ -1291,6 +1323,19 @@ hbugks_status hbugks_harmonic_noalloc(int nx, int ny, int nu, int nv, const doub
     k_dft<<<(int)((8 * nc + 127) / 128), 128, 0, s>>>(scratch, nt, (int)nc, k, re, im);
     HB_CK(cudaGetLastError());
     return HBUGKS_OK;
+}
+
+hbugks_status hbugks_test_expire_wait(hbugks_t h)
+{
+    if (!h) return HBUGKS_EINVAL;
+    return dispatch(h, [&](auto& im) -> hbugks_status {
+        hbugks_status rc = begin(h);
+        if (rc) return rc;
+        const int one = 1;
+        HB_CK(cudaMemcpyAsync(im.d_err + 1, &one, sizeof(int), cudaMemcpyHostToDevice, h->s));
+        HB_CK(cudaStreamSynchronize(h->s));
+        return end(h);
+    });
 }
 
 hbugks_status hbugks_get_tile_shape(hbugks_t h, int case_index, int* tx, int* ty)

@@ -131,9 +131,12 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bars[S], empty[S];
     __shared__ T sacc[NWC][4][NM];
+    __shared__ int abort_flag;                               // set by the first warp whose wait runs out
     const int cs = find_case(B.off, B.ncases, blockIdx.x);
     const CaseDev<T>& cd = B.cases[cs];
     if (!cd.st->active) return;
+    // another CTA may set the error word while this one starts: decide for the whole CTA at once
+    if (__syncthreads_or(*(volatile int*)cd.err != 0)) return;
     const int lb = blockIdx.x - B.off[cs];
     const int ntx = (cd.nx + TX - 1) / TX, nty = (cd.ny + TY - 1) / TY;
     const int tx = lb % ntx, ty = (lb / ntx) % nty, n = lb / (ntx * nty);
@@ -143,8 +146,10 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
     const int ti = warp % TX, tj = warp / TX, i = i0 + ti, j = j0 + tj;
     const bool valid = i < nx && j < ny;
     for (int k = lane; k < 4 * NM; k += 32) sacc[warp][k / NM][k % NM] = T(0);
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
         for (int k = 0; k < S; ++k) mbar_init(empty + k, NWC);   // one arrival per warp: slot read
+    }
     mbar_setup(bars, S);
     // staged rectangle: columns i0-1 .. i0+TX, rows j0-1 .. j0+TY; S buffers [G][h, b][NR][32] in a ring
     constexpr size_t blk = (size_t)NR * VB;
@@ -176,6 +181,13 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
     };
     if (warp == 0)
         for (int k = 0; k < S - 1 && k < nchunk; ++k) issue(k);
+    int issued = min(S - 1, nchunk);                         // chunks warp 0 has issued (kept on warp 0)
+    // a wait ran out: warp 0, which issued the copies, waits (bounded) for every chunk from k on that it has not
+    // seen complete, so that none still lands in shared memory after the CTA exits; the other warps just leave
+    auto give_up = [&](int k) {
+        if (warp == 0)
+            for (int q = k; q < issued; ++q) mbar_drain(&bars[q % S], (uint32_t)((q / S) & 1));
+    };
 
     // the warp's cell: neighbours, spacings, half widths (uniform over the warp)
     const bool hm = i > 0, hp = i < nx - 1, vm = j > 0, vp = j < ny - 1, sx = nx > 1, sy = ny > 1;
@@ -212,10 +224,17 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
     for (int k = 0; k < nchunk; ++k) {
         if (warp == 0 && k + S - 1 < nchunk) {
             const int kk = k + S - 1;
-            if (kk >= S && !mbar_wait(&empty[kk % S], (uint32_t)((kk / S - 1) & 1), err)) return;
+            if (kk >= S && !mbar_wait(&empty[kk % S], (uint32_t)((kk / S - 1) & 1), err, &abort_flag)) {
+                give_up(k);
+                return;
+            }
             issue(kk);
+            issued = kk + 1;
         }
-        if (!mbar_wait(&bars[k % S], (uint32_t)((k / S) & 1), err)) return;
+        if (!mbar_wait(&bars[k % S], (uint32_t)((k / S) & 1), err, &abort_flag)) {
+            give_up(k);
+            return;
+        }
         const T* cb = buf + (size_t)(k % S) * G * 2 * blk;
         const int vb0 = k * G, gk = min(G, nvb - vb0);
         if (valid) {
@@ -373,6 +392,9 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
     const int cs = find_case(B.off, B.ncases, blockIdx.x);
     const CaseDev<T>& cd = B.cases[cs];
     if (!cd.st->active) return;
+    // another CTA may set the error word while this one starts: decide for the whole CTA at once
+    if (__syncthreads_or(*(volatile int*)cd.err != 0)) return;
+    const bool expire = *(volatile const int*)cd.expire != 0;
     const int nvb = cd.nvb, nx = cd.nx, ny = cd.ny;
     // CTA order: velocity block fastest (the CTAs of one tile share its parameters in L2), then tiles in
     // strips of SROWS tile rows, column by column (neighbour tiles, whose halos overlap, run close in time)
@@ -492,8 +514,18 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
 
     for (int s = 0; s <= nt; ++s) {
         if (warp == 0 && s < nt) issue(s + 1);
-        const int fail = !mbar_wait(&bars[s & 1], (uint32_t)((s >> 1) & 1), err);
-        if (__syncthreads_or(fail)) return;
+        // the test hook reports the first wait as expired only after it has completed
+        const int fail = !mbar_wait(&bars[s & 1], (uint32_t)((s >> 1) & 1), err) || expire;
+        if (__syncthreads_or(fail)) {
+            // every thread agrees; warp 0, which issued them, waits (bounded) for batches s and s + 1, so that
+            // no bulk copy still lands in shared memory after the CTA exits
+            if (threadIdx.x == 0 && expire) atomicExch(err, 1);
+            if (warp == 0) {
+                mbar_drain(&bars[s & 1], (uint32_t)((s >> 1) & 1));
+                if (s < nt) mbar_drain(&bars[(s + 1) & 1], (uint32_t)(((s + 1) >> 1) & 1));
+            }
+            return;
+        }
         if (s < nt) {
             // ---- pass 1, level s: reconstruction and downwind-face fluxes
             const int n = s;

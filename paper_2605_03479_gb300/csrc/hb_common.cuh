@@ -97,7 +97,10 @@ struct CaseDev {
     double* stage;                     // conversion staging (>= nc * nvel_pad doubles)
     CaseStatus* st;
     const double* tol;                 // shared residual target of the handle
-    int* err;                          // device error word of the handle (1: a bounded wait expired)
+    int* err;                          // device error word of the handle (1: a bounded wait expired); every
+                                       // kernel of the iteration returns at once while it is set
+    const int* expire;                 // test hook of the handle: nonzero makes the micro update report its
+                                       // first completed wait as expired (no copy in flight is abandoned)
 };
 
 template <typename T>
@@ -172,14 +175,84 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase)
     return ok != 0;
 }
 
-// Wait for phase `phase` of `bar` with an iteration limit; on expiry record the failure in *err and return false.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, int* err)
+// nanoseconds of the GPU's global timer
+__device__ __forceinline__ uint64_t global_ns()
 {
-    for (int it = 0; it < (1 << 24); ++it)
-        if (mbar_try_wait(bar, phase)) return true;
-    atomicExch(err, 1);
-    return false;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
+
+// A bulk copy lands in microseconds; a wait that lasts this long has failed.
+constexpr uint64_t WAIT_LIMIT_NS = 500000000ull;
+
+// Wait for phase `phase` of `bar`, bounded by elapsed time.  On expiry record the failure in *err (and in the
+// CTA's abort flag, if given) and return false.  A wait also gives up, without recording anything, once another
+// warp of the CTA has set the abort flag, so that one failed wait stops the whole CTA within one limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, int* err, volatile int* abort = nullptr)
+{
+    if (mbar_try_wait(bar, phase)) return true;
+    const uint64_t t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try_wait(bar, phase)) return true;
+        if ((it & 31) == 0) {
+            if (abort && *abort) return false;
+            if (global_ns() - t0 > WAIT_LIMIT_NS) {
+                atomicExch(err, 1);
+                if (abort) *abort = 1;
+                return false;
+            }
+        }
+    }
+}
+
+// After a failed wait: bounded wait for a batch of bulk copies that was issued and not yet seen complete, so
+// that no copy is still writing into the CTA's shared memory when it exits.  If that wait runs out too (the
+// copies themselves failed), the CTA exits regardless; the handle's error word is already set.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t phase)
+{
+    const uint64_t t0 = global_ns();
+    for (unsigned it = 0;; ++it) {
+        if (mbar_try_wait(bar, phase)) return;
+        if ((it & 31) == 31 && global_ns() - t0 > WAIT_LIMIT_NS) return;
+    }
+}
+
+// ------------------------------------------------------------------ (h, b) pairs and packed arithmetic
+// The reduced distributions h and b of one velocity go through the same transport, reconstruction, spectral and
+// update arithmetic, so they are stored and processed as a pair.  For float a pair is one 64-bit register pair
+// and every operation below is a single packed FP32x2 instruction of sm_100+ (both halves rounded as the
+// scalar instruction would); for double they are two scalar operations.
+template <typename T> struct PairOf;
+template <> struct PairOf<float> { using type = float2; };
+template <> struct PairOf<double> { using type = double2; };
+template <typename T> using P2 = typename PairOf<T>::type;
+
+__device__ __forceinline__ float2 pk(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ double2 pk(double x, double y) { return make_double2(x, y); }
+__device__ __forceinline__ float2 bc(float x) { return make_float2(x, x); }
+__device__ __forceinline__ double2 bc(double x) { return make_double2(x, x); }
+
+__device__ __forceinline__ uint64_t f2u(float2 a) { return *reinterpret_cast<uint64_t*>(&a); }
+__device__ __forceinline__ float2 u2f(uint64_t a) { return *reinterpret_cast<float2*>(&a); }
+
+// a * b + c
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c)
+{
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(d);
+}
+__device__ __forceinline__ double2 psub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 
 template <typename T> __device__ __forceinline__ T t_expm1(T x);
 template <> __device__ __forceinline__ double t_expm1<double>(double x) { return expm1(x); }

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
 {
     int cs = find_case(B.off, B.ncases, blockIdx.x);
     const CaseDev<T>& cd = B.cases[cs];
-    if (!cd.st->active) return;
+    if (!cd.st->active || *(volatile int*)cd.err) return;
     const int item = (blockIdx.x - B.off[cs]) * blockDim.x + threadIdx.x;
     const int nt = cd.nt;
     if (item >= cd.nf * nt) return;
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(128) k_tables(Batch<T> B)
 {
     const int cs = find_case(B.off, B.ncases, blockIdx.x);
     const CaseDev<T>& cd = B.cases[cs];
-    if (!cd.st->active) return;
+    if (!cd.st->active || *(volatile int*)cd.err) return;
     const int lane = threadIdx.x & 31;
     const int item = (blockIdx.x - B.off[cs]) * 4 + (threadIdx.x >> 5);   // cell-level pair, c * nt + n
     const int nt = cd.nt, nuv = cd.nu + cd.nv;
@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(K3_THREADS) k3_macro(Batch<T> B)
 {
     int cs = find_case(B.off, B.ncases, blockIdx.x);
     const CaseDev<T>& cd = B.cases[cs];
-    if (!cd.st->active) return;
+    if (!cd.st->active || *(volatile int*)cd.err) return;
     const int lb = blockIdx.x - B.off[cs];
     const int c = lb * K3_THREADS + threadIdx.x;
     const int nt = cd.nt, nc = cd.nc;
@@ -638,7 +638,7 @@ __global__ void k5_finish(const CaseDev<T>* cases, int ncases, const int* k3off)
     if (cs >= ncases) return;
     const CaseDev<T>& cd = cases[cs];
     CaseStatus* st = cd.st;
-    if (!st->active) return;
+    if (!st->active || *(volatile int*)cd.err) return;   // a failed wait leaves the iteration unfinished
     const int nb = k3off[cs + 1] - k3off[cs];
     __shared__ double part[4][32];
     const int lane = threadIdx.x;      // 32 threads

@@ -61,7 +61,7 @@ EXPORTED = ("hbugks_workspace_bytes", "hbugks_create", "hbugks_destroy", "hbugks
             "hbugks_residual_history", "hbugks_get_level_fields", "hbugks_get_harmonic", "hbugks_iteration_count",
             "hbugks_status_string", "hbugks_enqueue_iterations", "hbugks_profile_kernels",
             "hbugks_harmonic_noalloc", "hbugks_launches_per_iteration", "hbugks_get_tile_shape",
-            "hbugks_set_tile_shape", "hbugks_cuda_error_string")
+            "hbugks_set_tile_shape", "hbugks_cuda_error_string", "hbugks_test_expire_wait")
 
 
 def lib():
@@ -101,6 +101,7 @@ def lib():
             L.hbugks_cuda_error_string.restype = C.c_char_p
             L.hbugks_get_tile_shape.argtypes = [vp, i, C.POINTER(i), C.POINTER(i)]
             L.hbugks_set_tile_shape.argtypes = [vp, i, i, i]
+            L.hbugks_test_expire_wait.argtypes = [vp]
             for name in EXPORTED:
                 if name not in ("hbugks_workspace_bytes", "hbugks_destroy", "hbugks_iteration_count",
                                 "hbugks_status_string", "hbugks_cuda_error_string"):
@@ -233,8 +234,12 @@ class Solver:
         its = (C.c_int * n)()
         res = np.zeros((n, 4))
         rc = lib().hbugks_iterate(self.h, int(max_iters), float(tol_rho), its, _dp(res))
-        _check(rc, "hbugks_iterate", allow=(OK, NOT_CONVERGED, DIVERGED))
+        _check(rc, "hbugks_iterate", allow=(OK, NOT_CONVERGED, DIVERGED, TIMEOUT))
         return rc, np.array(its[:], dtype=np.int64), res
+
+    def test_expire_wait(self):
+        """Make the next iteration's micro update report its first (completed) wait as expired."""
+        _check(lib().hbugks_test_expire_wait(self.h), "hbugks_test_expire_wait")
 
     def enqueue_iterations(self, n: int):
         _check(lib().hbugks_enqueue_iterations(self.h, int(n)), "hbugks_enqueue_iterations")

@@ -32,6 +32,9 @@ def test_reference_line_matches_the_gpu_arm_contract():
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     assert cb["host"]["nproc"] >= 1 and cb["host"]["machine"]
+    assert cb["cores"] == bench.usable_cores() == line["sample_config"]["processes"]
+    sc = line["sample_config"]                     # what each step actually ran
+    assert sc["cells"] == [8, 8] and sc["velocities"] == [24, 24] and sc["n_levels"] == 3
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
 

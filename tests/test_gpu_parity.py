@@ -233,3 +233,71 @@ def test_implicit_spectral_matches_oracle(hb, name, factory, niter, precision):
         close(g[0], o[0], init[0], 2e-5, 2e-9)
         close(g[1], o[1], init[1], 2e-5, 2e-7)
         close(g[2], o[2], init[2], 2e-5, 2e-7)
+
+
+# The configuration of the large thermal benchmark (64 x 64 midpoint velocities on [-4, 4], N_H = 5, Kn 0.05,
+# St 5, Pr 2/3, bottom wall T0 (1 + 0.5 sin wt)) on a 16 x 16 mesh: four interior tiles of 4 x 4 cells (the
+# paired first pass), wall and corner tiles, every spectral offset d = 1..5, from a seeded state.  Each precision
+# runs with two pinned micro-update tiles (FP64 needs the smaller tiles at N_T = 11 for shared memory).
+_ORACLE_CACHE = {}
+
+
+def _bench_grid_case():
+    return I.make_case("bench_grid16", 16, 64, kn=0.05, st=5.0, nh=5, pr=2 / 3, drive="thermal", amp=0.5)
+
+
+def _oracle_run(key, case, niter, seed):
+    if key not in _ORACLE_CACHE:
+        W0, h0, b0 = I.initial_state(case, seed=seed)
+        P = O.Problem(case)
+        W, h, b = W0.copy(), h0.copy(), b0.copy()
+        res = O.iterate(P, W, h, b, niter)
+        _ORACLE_CACHE[key] = ((W0, h0, b0), (W, h, b), res)
+    return _ORACLE_CACHE[key]
+
+
+@pytest.mark.parametrize("precision,tile", [(0, (4, 2)), (0, (2, 2)), (1, (4, 4)), (1, (8, 4))],
+                         ids=["fp64_tile4x2", "fp64_tile2x2", "fp32split_tile4x4", "fp32split_tile8x4"])
+def test_bench_grid_nh5_matches_oracle(hb, precision, tile):
+    case = _bench_grid_case()
+    init, o, res_o = _oracle_run("bench_grid16", case, 2, seed=7)
+    case.precision = precision
+    s = hb.Solver(case)
+    s.set_tile_shape(0, *tile)
+    assert s.tile_shape(0) == tile
+    s.set_state(0, *init)
+    rc, its, res_g = s.iterate(2)
+    g = s.get_state(0)
+    s.destroy()
+    if precision == 0:
+        for k in range(3):
+            close(g[k], o[k], init[k], 1e-10, 1e-13)
+        np.testing.assert_allclose(res_g[0], res_o[-1], rtol=1e-8, atol=1e-16)
+    else:
+        close(g[0], o[0], init[0], 2e-5, 2e-9)
+        close(g[1], o[1], init[1], 2e-5, 2e-7)
+        close(g[2], o[2], init[2], 2e-5, 2e-7)
+
+
+# the two level counts no other case uses (N_T = 9 and 13), both precisions
+CASES_NH46 = [
+    ("nh4_thermal", lambda: I.make_case("n4", 9, 12, kn=0.1, st=2.0, nh=4, pr=2 / 3, drive="thermal", amp=0.3,
+                                        ncell_y=6), 3),
+    ("nh6_shear", lambda: I.make_case("n6", 6, 10, kn=0.3, st=1.0, nh=6, pr=2 / 3, drive="shear", amp=0.02,
+                                      ncell_y=9), 3),
+]
+
+
+@pytest.mark.parametrize("name,factory,niter", CASES_NH46, ids=[c[0] for c in CASES_NH46])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nh4_nh6_match_oracle(hb, name, factory, niter, precision):
+    case = factory()
+    case.precision = precision
+    init, g, o, res_g, res_o = run_both(hb, case, niter)
+    if precision == 0:
+        for k in range(3):
+            close(g[k], o[k], init[k], 1e-10, 1e-13)
+    else:
+        close(g[0], o[0], init[0], 2e-5, 2e-9)
+        close(g[1], o[1], init[1], 2e-5, 2e-7)
+        close(g[2], o[2], init[2], 2e-5, 2e-7)

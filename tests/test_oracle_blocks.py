@@ -258,3 +258,18 @@ def test_tanh_mesh_ratio():
     r = d[1:] / d[:-1]
     assert np.max(np.maximum(r, 1 / r)) == pytest.approx(1.1, rel=1e-9)
     np.testing.assert_allclose(d, d[::-1], rtol=1e-12)
+
+
+@pytest.mark.parametrize("nt", [3, 5, 7, 11])
+def test_harmonics_sign_and_scale_of_eq_dft_general(nt):
+    """Eq. dft_general with the kernel e^{-i k omega t_n}, omega t_n = 2 pi n / N_T: samples of
+    A cos(omega t + phi) + B sin(2 omega t) + C give C at k = 0, (A/2) e^{+i phi} at k = 1 and -i B/2 at k = 2
+    (a transform with the opposite sign of the exponent gives the conjugates; one without the 1/N_T scales them)."""
+    th = 2 * math.pi * np.arange(nt) / nt
+    for A, phi, B, Cc in ((0.8, 0.3, 0.1, 1.5), (1.3, -1.1, -0.25, -0.2), (0.5, 2.5, 0.0, 0.0)):
+        q = A * np.cos(th + phi) + (B * np.sin(2 * th) if nt >= 5 else 0.0) + Cc
+        H = O.harmonics(np.stack([np.array([x]) for x in q]))[:, 0]
+        assert abs(H[0] - Cc) < 1e-14
+        assert abs(H[1] - 0.5 * A * np.exp(1j * phi)) < 1e-14
+        if nt >= 5:
+            assert abs(H[2] - (-0.5j * B)) < 1e-14

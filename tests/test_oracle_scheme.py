@@ -337,6 +337,57 @@ def test_harmonic_balance_matches_time_marching():
     assert errs[1] < errs[0], errs
 
 
+def _first_order_hb(cfl, amp):
+    c = I.tiny_case(ncell=4, nvel=8, kn=1.0, st=1.0, nh=1, pr=1.0, drive="shear", amp=amp, cfl=cfl)
+    W, h, b = I.initial_state(c)
+    P = O.Problem(c, dt_fixed=float(O.cell_steps(O.Problem(c), W).min()), first_order=True)
+    for _ in range(200):
+        if O.iterate(P, W, h, b, 500)[-1, 0] < 1e-17:
+            break
+    return O.harmonics(np.stack([O.fields(P, h, b, n) for n in range(3)]))
+
+
+def _first_order_td(steps_per_level, amp, periods=25):
+    nsub = 3 * steps_per_level
+    c = I.tiny_case(ncell=4, nvel=8, kn=1.0, st=1.0, nh=0, pr=1.0, drive="shear", amp=amp)
+    W, h, b = I.initial_state(c)
+    steps = [O.Problem(c, theta0=2 * math.pi * (s + 0.5) / nsub, dt_fixed=2 * math.pi / nsub, first_order=True)
+             for s in range(nsub)]
+    P0 = O.Problem(c)
+    for _ in range(periods):
+        samples = []
+        for s in range(nsub):
+            if s % steps_per_level == 0:
+                samples.append(O.fields(P0, h, b, 0))
+            O.iterate(steps[s], W, h, b, 1)
+    return O.harmonics(np.stack(samples))
+
+
+@pytest.mark.slow
+def test_harmonic_balance_and_time_marching_converge_together_under_refinement():
+    """With the first-order (unlimited) reconstruction the scheme is linear in the drive, so the periodic state
+    holds only the harmonics of the lid and N_H = 1 represents it exactly (N_H = 1 and 2 agree to 4e-5).  Then
+    the HB fixed point and the periodic state of explicit time marching differ only by discretisation error:
+    refining both the HB pseudo-step (CFL 0.8 -> 0.2) and the physical step (120 -> 240 -> 480 steps per level)
+    halves the gap of the first harmonic of U each time (first order in the physical step) down to below the
+    0.3 % the paper reports between the two (Sec 3.2.3), while the pseudo-step moves the HB answer far less.
+    (With the van Leer limiter the scheme is only positively homogeneous: the limiter makes harmonics of the
+    same relative size at any amplitude, and the HB answer then also depends on N_H at the 1 % level.)"""
+    amp = 0.001
+    Hhb = {cfl: _first_order_hb(cfl, amp)[1, 1] for cfl in (0.8, 0.2)}
+    gaps = []
+    for spl in (120, 240, 480):
+        Htd = _first_order_td(spl, amp)[1, 1]
+        gaps.append([np.max(np.abs(Htd - Hhb[cfl])) / np.max(np.abs(Hhb[cfl])) for cfl in (0.8, 0.2)])
+    gaps = np.array(gaps)
+    for k in (1, 2):
+        ratio = gaps[k - 1] / gaps[k]
+        assert np.all((ratio > 1.7) & (ratio < 2.3)), gaps
+    assert gaps[-1, 1] < 3e-3, gaps
+    hb_move = np.max(np.abs(Hhb[0.8] - Hhb[0.2])) / np.max(np.abs(Hhb[0.2]))
+    assert hb_move < 1e-3 and hb_move < 0.1 * gaps[0, 1], (hb_move, gaps)
+
+
 # ------------------------------------------------------------------ spectral source at the new iterate
 
 def _run(case, implicit, niter, dt_fixed=0.0):
@@ -406,7 +457,11 @@ def test_collisionless_limits_of_the_oscillating_lid():
     Ut, tt, Uc, ratio = _lid_amplitudes(30.0, 400)
     assert abs(Ut - 0.5) < 0.02 * 0.5, Ut
     assert abs(tt - 1 / math.sqrt(math.pi)) < 0.02 / math.sqrt(math.pi), tt
-    assert abs(np.angle(Uc)) < 0.15, Uc                    # in phase with the lid (measured lag 0.07 rad)
-    assert abs(np.angle(-ratio)) < 0.15, ratio             # stress opposes the gas velocity
+    # signed phases under Eq. dft_general (kernel e^{-i k omega t_n}, the lid's own harmonic real and positive):
+    # the gas follows the lid causally, so its velocity lags it, a small negative angle (measured -0.074 rad);
+    # the stress opposes the gas velocity and leads it slightly (measured +0.083 rad).  A DFT with the opposite
+    # sign of the exponent flips both signs.
+    assert -0.15 < np.angle(Uc) < 0.0, Uc
+    assert 0.0 < np.angle(-ratio) < 0.15, ratio
     Ut, tt, _, _ = _lid_amplitudes(0.5, 800)
     assert abs(Ut - 0.5) > 0.1 * 0.5 and abs(tt - 1 / math.sqrt(math.pi)) > 0.1 / math.sqrt(math.pi), (Ut, tt)
