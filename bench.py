@@ -319,14 +319,24 @@ def hb_versus_td(args):
     from paper_2605_03479_gb300 import inputs as I
     orders, budget, atol = args.hb_vs_td, args.ttr_budget, args.hb_vs_td_abs
     sts = [float(x) for x in args.hb_vs_td_st.split(",")]
-    runs = [(d, st, 1 if d == "shear" else 2) for d in ("shear", "thermal") for st in sts]
+    runs = [(d, st, 1 if d == "shear" else 2) for d in args.hb_vs_td_drives.split(",") for st in sts]
 
     def mk(drive, st, nh):
-        # the paper's two cavities (Sec 3.1, 3.2): lid U_a cos(wt); top wall T0 (1 + 0.3 cos wt), N_H = 2
-        c = I.make_case(f"{drive}32_v24", 32, 24, kn=0.1, st=st, nh=nh, pr=1.0 if drive == "shear" else 2 / 3,
-                        drive="shear" if drive == "shear" else "rest", amp=0.01, precision=args.precision)
-        if drive == "thermal":
-            c.walls[I.TOP][7] = 0.3                  # T_re: 0.3 T0 cos(theta)
+        if args.hb_vs_td_mesh == "paper":
+            # the paper's own cavities (Sec 3.1.1, 3.2): 90 rows refined to 0.001 H at every wall; lid
+            # 0.0015 cos(wt) with 28 x 28 Gauss-Hermite velocities at Kn 0.1; top wall T0 (1 + 0.3 cos wt)
+            # with the 64 x 64 midpoint grid
+            if drive == "shear":
+                c = I.paper_shear_case(0.1, st, 1.0, nh=nh, precision=args.precision)
+            else:
+                c = I.paper_thermal_case(0.1, st, nh=nh, precision=args.precision)
+        else:
+            # the paper's two cavities (Sec 3.1, 3.2) on a coarse uniform mesh: lid U_a cos(wt); top wall
+            # T0 (1 + 0.3 cos wt), N_H = 2
+            c = I.make_case(f"{drive}32_v24", 32, 24, kn=0.1, st=st, nh=nh, pr=1.0 if drive == "shear" else 2 / 3,
+                            drive="shear" if drive == "shear" else "rest", amp=0.01, precision=args.precision)
+            if drive == "thermal":
+                c.walls[I.TOP][7] = 0.3                  # T_re: 0.3 T0 cos(theta)
         c.spectral_implicit = args.spectral_implicit if nh > 0 else 0
         return c
 
@@ -338,17 +348,18 @@ def hb_versus_td(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         its, r1, r, t_rel, t_abs = 0, 0.0, 0.0, None, None
+        chunk = 64
         while True:
-            s.iterate(16)
-            its += 16
-            h_ = s.residual_history(0, 16)[:, 0]
+            s.iterate(chunk)
+            its += chunk
+            h_ = s.residual_history(0, chunk)[:, 0]
             if r1 == 0.0 and np.any(h_ > 0):
                 r1 = float(h_[h_ > 0][0])
             r = float(h_[-1])
             el = time.perf_counter() - t0
             if t_rel is None and r1 > 0 and r <= r1 * 10.0 ** (-orders):
                 t_rel = (el, its)
-            if t_abs is None and its > 16 and r <= atol:
+            if t_abs is None and its > chunk and r <= atol:
                 t_abs = (el, its)
             if (t_rel and t_abs) or el > budget or not np.isfinite(r):
                 break
@@ -392,7 +403,8 @@ def hb_versus_td(args):
         ratio = lambda k: (out["td"][k] / out["hb"][k]) if out["td"][k] and out["hb"][k] else None
         line = {"metric": "wall time to a density-residual drop, HB-UGKS vs explicit time-domain UGKS",
                 "orders": orders, "absolute": atol, "unit": "s",
-                "case": f"{drive} cavity 32x32 cells, 24x24 velocities, Kn 0.1, St {st:g}",
+                "case": (f"{drive} cavity {c.nx}x{c.ny} cells ({args.hb_vs_td_mesh} mesh), {c.nu}x{c.nv} velocities, "
+                         f"Kn {c.kn:g}, St {st:g}, N_H {nh}"),
                 "dtype": "f32-split" if args.precision else "f64",
                 "hb_spectral_source": "new iterate (implicit)" if args.spectral_implicit else "old iterate (as printed)",
                 "hb": out["hb"], "td": out["td"],
@@ -421,6 +433,9 @@ def main():
     ap.add_argument("--precision", type=int, default=0, help="precision of --hb-vs-td (0 FP64, 1 FP32-split)")
     ap.add_argument("--hb-vs-td-abs", type=float, default=1e-8, help="absolute density residual for --hb-vs-td")
     ap.add_argument("--hb-vs-td-st", default="2,30", help="Strouhal numbers for --hb-vs-td")
+    ap.add_argument("--hb-vs-td-mesh", choices=("coarse32", "paper"), default="coarse32",
+                    help="--hb-vs-td cavities: 32x32 uniform cells, or the paper's 90-row wall-refined mesh")
+    ap.add_argument("--hb-vs-td-drives", default="shear,thermal", help="--hb-vs-td drives to run")
     ap.add_argument("--spectral-implicit", type=int, default=0,
                     help="--hb-vs-td, --ttr: HB with the spectral source at the new pseudo-time iterate (1)")
     args = ap.parse_args()
@@ -492,7 +507,9 @@ def main():
     ms = slowest_rank_ms(e0.elapsed_time(e1) / args.steps, dist, dev)
     upd = sum(c.updates_per_iteration() for c in cases)
     value = job_updates_per_s(upd, world, ms)
-    launches = s.launches_per_iteration() * args.steps + 1
+    # per iteration: the iteration's kernels and the device-side loop test; per call: the status reset and the
+    # kernel that sets the loop count
+    launches = s.launches_per_iteration() * args.steps + 2
 
     # per-kernel times (CUDA events around each launch on the kernels' stream), roofline of the top kernel
     kms = s.profile_kernels(3)

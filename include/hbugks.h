@@ -221,6 +221,15 @@ HBUGKS_API hbugks_status hbugks_harmonic_noalloc(int nx, int ny, int nu, int nv,
 HBUGKS_API hbugks_status hbugks_get_tile_shape(hbugks_t h, int case_index, int* tx, int* ty);
 HBUGKS_API hbugks_status hbugks_set_tile_shape(hbugks_t h, int case_index, int tx, int ty);
 
+/* Copy the state of case src_case of handle src into case dst_case of handle dst, converting between the two
+ * handles' precisions.  The use it serves is mixed-precision refinement: iterate an FP32-split handle close to
+ * convergence, copy its state into an FP64 handle of the same case, and let a few FP64 iterations remove the
+ * rounding floor of the FP32 storage (the fixed point is the FP64 one).  Both cases must have the same mesh,
+ * velocity grid and N_T (HBUGKS_EINVAL otherwise); walls and physics are those of dst.  Runs after all work
+ * enqueued on src's stream, on dst's stream, and resets dst's iteration count for that case.  Both handles must
+ * live on the current device.  The paper has no counterpart (a precision choice of this library). */
+HBUGKS_API hbugks_status hbugks_copy_state(hbugks_t dst, int dst_case, hbugks_t src, int src_case);
+
 /* Failure-path test hook.  Every device-side wait of the iteration kernels (a bulk copy into shared memory
  * completing on an mbarrier) is bounded by elapsed time: on expiry the kernel sets the handle's error word, its
  * CTA waits (bounded) for the copies it has issued and exits, every later kernel of the iteration returns
@@ -233,6 +242,14 @@ HBUGKS_API hbugks_status hbugks_test_expire_wait(hbugks_t h);
 
 /* Number of kernel launches one iteration enqueues for this handle. */
 HBUGKS_API int hbugks_launches_per_iteration(hbugks_t h);
+
+/* How hbugks_iterate and hbugks_enqueue_iterations run their iterations.  mode 0 (default): one launch of a
+ * CUDA graph whose conditional while node repeats one iteration and a one-thread loop test until the count is
+ * spent, every case has converged or diverged, or a device wait has failed; the host reads the statuses once, at
+ * the end.  mode 1: graphs of 16 iterations launched from the host, which reads the statuses after each (the
+ * earlier design, kept for comparison).  Both run the same kernels and give bitwise the same state.  The paper
+ * has no counterpart. */
+HBUGKS_API hbugks_status hbugks_set_loop_mode(hbugks_t h, int mode);
 
 #ifdef __cplusplus
 }

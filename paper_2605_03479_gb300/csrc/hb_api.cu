@@ -85,6 +85,7 @@ struct HostCase {
     std::vector<double> vfac;
     int k1b, k2b, k3b, k4b, ksb, ktb;
     int k4shape;
+    int k1sep;                      // face sums by v-moments: no zero node, every sign class 1..32 u-nodes wide
 };
 
 // K1 tile (TX x TY cells, one warp each) and velocity blocks staged per pass, per storage precision
@@ -97,6 +98,11 @@ template <typename T>
 constexpr size_t k1_smem_of()
 {
     return k1_cells_smem<T, K1_TX<T>, K1_TY<T>, K1_G<T>, K1_S<T>>();
+}
+template <typename T, bool SEP>
+constexpr auto k1_kernel()
+{
+    return k1_cells<T, K1_TX<T>, K1_TY<T>, K1_G<T>, K1_S<T>, SEP>;
 }
 
 // K4 tile shapes (TX, TY, warps per CTA)
@@ -193,6 +199,16 @@ void fill_host(HostCase& h, const hbugks_case& c)
     }
     h.nvp = (int)h.vcan.size();
     h.nvb = h.nvp / VB;
+    {
+        int upos = 0, uneg = 0, zero = 0;
+        for (int iu = 0; iu < h.nu; ++iu) {
+            const double uu = c.vgrid.u[iu];
+            upos += uu > 0; uneg += uu < 0; zero += uu == 0;
+        }
+        for (int jv = 0; jv < h.nv; ++jv) zero += c.vgrid.v[jv] == 0;
+        // in a class of k u-nodes with k dividing 32, lane l of every block holds u-node l mod k
+        h.k1sep = !zero && upos > 0 && uneg > 0 && 32 % upos == 0 && 32 % uneg == 0;
+    }
     h.nh = c.phys.n_harmonics;
     h.nt = 2 * h.nh + 1;
     h.nfx = h.ny * (h.nx + 1);
@@ -254,14 +270,14 @@ void layout_case(Carver& cv, const HostCase& h, CaseDev<T>& d)
     d.rdx = cv.take<double>(h.nx); d.rdy = cv.take<double>(h.ny);
     d.vu = cv.take<double>(h.nvp); d.vv = cv.take<double>(h.nvp); d.vw = cv.take<double>(h.nvp);
     d.tu = cv.take<T>(h.nvp); d.tv = cv.take<T>(h.nvp); d.tw = cv.take<T>(h.nvp); d.thref = cv.take<T>(h.nvp);
+    d.twu = cv.take<T>(h.nvp); d.twv = cv.take<T>(h.nvp);
     d.u1 = cv.take<double>(h.nu); d.wu1 = cv.take<double>(h.nu);
     d.v1 = cv.take<double>(h.nv); d.wv1 = cv.take<double>(h.nv);
     d.tu1 = cv.take<T>(h.nu); d.tv1 = cv.take<T>(h.nv);
     d.refmom = cv.take<double>(5 * 13);
     const size_t ns = (size_t)h.nvb * h.nc * h.nt * VB;
     for (int k = 0; k < 2; ++k) {
-        d.dh[k] = cv.take<T>(ns);
-        d.db[k] = cv.take<T>(ns);
+        d.f[k] = cv.take<P2<T>>(ns);
         d.W[k] = cv.take<double>((size_t)h.nt * h.nc * 4);
     }
     d.dG = cv.take<double>(h.nc);
@@ -313,6 +329,7 @@ struct Impl {
     CaseStatus* d_status = nullptr;
     double* d_tol = nullptr;
     int* d_err = nullptr;            // [0] error word (a bounded wait expired), [1] test hook: expire the next wait
+    int* d_loop = nullptr;           // iterations left in the device-side loop of the current call
     int* d_off = nullptr;            // [table][ncases + 1]
     int* d_tune_off = nullptr;       // block offsets of a single-case launch (autotuning)
     std::vector<int> off_host;
@@ -328,6 +345,8 @@ struct hbugks_solver {
     cudaStream_t s = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t g1 = nullptr, gN = nullptr;
+    cudaGraphExec_t gW = nullptr;     // device-side loop: a while node over one iteration and the loop test
+    int loop_mode = 0;                // 0: device-side loop (gW), 1: host-polled graphs of CHUNK iterations
     char* ws = nullptr;
     size_t bytes = 0;
     Impl<float>* f = nullptr;
@@ -365,11 +384,13 @@ size_t plan(Impl<T>& im, int ncases, const hbugks_case* cases, char* base)
     im.d_status = cv.take<CaseStatus>(ncases);
     im.d_tol = cv.take<double>(1);
     im.d_err = cv.take<int>(2);
+    im.d_loop = cv.take<int>(2);
     im.d_tune_off = cv.take<int>(2);
     // launch specs: K1 per shape, K2, K3, tables, K4 per shape; plus the step kernel (state setting only)
     im.specs.clear();
     auto add = [&](int kind, int shape) { im.specs.push_back(LaunchSpec{kind, shape, (int)im.specs.size(), 0, 0}); };
     add(0, 0);
+    add(0, 1);
     add(1, 0);
     add(2, 0);
     im.k3_table = (int)im.specs.size() - 1;
@@ -404,7 +425,7 @@ void fill_offsets(Impl<T>& im, int ncases)
             const HostCase& h = im.hc[k];
             int nb = 0;
             switch (sp.kind) {
-                case 0: nb = h.k1b; smem = k1_smem_of<T>(); break;
+                case 0: nb = h.k1sep == sp.shape ? h.k1b : 0; smem = k1_smem_of<T>(); break;
                 case 1: nb = h.k2b; break;
                 case 2: nb = h.k3b; break;
                 case 3: nb = h.ktb; break;
@@ -487,7 +508,8 @@ cudaError_t upload_case(const HostCase& h, const CaseDev<T>& d, cudaStream_t s, 
     for (int i = 0; i + 1 < h.nx; ++i) rdx[i] = 1.0 / (xc[i + 1] - xc[i]);
     for (int j = 0; j + 1 < h.ny; ++j) rdy[j] = 1.0 / (yc[j + 1] - yc[j]);
     std::vector<double> vu(h.nvp, 0.0), vv(h.nvp, 0.0), vw(h.nvp, 0.0);
-    std::vector<T> tu(h.nvp, T(0)), tv(h.nvp, T(0)), tw(h.nvp, T(0)), th(h.nvp, T(0));
+    std::vector<T> tu(h.nvp, T(0)), tv(h.nvp, T(0)), tw(h.nvp, T(0)), th(h.nvp, T(0)), twu(h.nvp, T(0)),
+        twv(h.nvp, T(0));
     double ref[5][13];
     memset(ref, 0, sizeof ref);
     std::vector<int> iu_(h.nvp, 0), iv_(h.nvp, 0);
@@ -498,6 +520,7 @@ cudaError_t upload_case(const HostCase& h, const CaseDev<T>& d, cudaStream_t s, 
         const double u = h.u[iu], v = h.v[jv], w = h.wu[iu] * h.wv[jv] * h.vfac[a];
         vu[a] = u; vv[a] = v; vw[a] = w;
         tu[a] = T(u); tv[a] = T(v); tw[a] = T(w); th[a] = T((1.0 / M_PI) * exp(-(u * u + v * v)));
+        twu[a] = T(h.wu[iu]); twv[a] = T(h.wv[jv] * h.vfac[a]);
         iu_[a] = iu; iv_[a] = jv;
     }
     for (int jv = 0; jv < h.nv; ++jv)
@@ -528,6 +551,8 @@ cudaError_t upload_case(const HostCase& h, const CaseDev<T>& d, cudaStream_t s, 
     if ((e = put(d.tv, tv.data(), sizeof(T) * h.nvp))) return e;
     if ((e = put(d.tw, tw.data(), sizeof(T) * h.nvp))) return e;
     if ((e = put(d.thref, th.data(), sizeof(T) * h.nvp))) return e;
+    if ((e = put(d.twu, twu.data(), sizeof(T) * h.nvp))) return e;
+    if ((e = put(d.twv, twv.data(), sizeof(T) * h.nvp))) return e;
     if ((e = put(d.u1, h.u.data(), sizeof(double) * h.nu))) return e;
     if ((e = put(d.wu1, h.wu.data(), sizeof(double) * h.nu))) return e;
     if ((e = put(d.v1, h.v.data(), sizeof(double) * h.nv))) return e;
@@ -597,10 +622,36 @@ __global__ void k_begin_call(CaseStatus* st, int ncases)
     st[k].iters_call = 0;
 }
 
-template <typename T>
-void launch_k1(int total, size_t smem, Batch<T> b, cudaStream_t s)
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
+// End of one pass of the device-side loop: one iteration fewer left; the loop goes on while iterations are left,
+// some case is still iterating (not converged, not diverged) and no device wait has failed.  Every pass
+// decrements the count, so the loop ends after at most the requested number of iterations.
+__global__ void k_loop_test(cudaGraphConditionalHandle hc, int* left, const CaseStatus* st, int ncases, const int* err)
 {
-    k1_cells<T, K1_TX<T>, K1_TY<T>, K1_G<T>, K1_S<T>><<<total, K1_TX<T> * K1_TY<T> * 32, smem, s>>>(b);
+    if (threadIdx.x != 0) return;
+    const int r = *left - 1;
+    *left = r;
+    int any = 0;
+    for (int k = 0; k < ncases; ++k) any |= st[k].active;
+    cudaGraphSetConditional(hc, (r > 0 && any && *(volatile const int*)err == 0) ? 1u : 0u);
+}
+
+// state of one case copied between handles of possibly different precision (same grid and velocity layout)
+template <typename TS, typename TD>
+__global__ void k_convert_state(const P2<TS>* src, P2<TD>* dst, size_t n)
+{
+    const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const P2<TS> a = src[k];
+    dst[k] = pk(TD(a.x), TD(a.y));
+}
+
+template <typename T>
+void launch_k1(int shape, int total, size_t smem, Batch<T> b, cudaStream_t s)
+{
+    if (shape == 1) k1_kernel<T, true>()<<<total, K1_TX<T> * K1_TY<T> * 32, smem, s>>>(b);
+    else k1_kernel<T, false>()<<<total, K1_TX<T> * K1_TY<T> * 32, smem, s>>>(b);
 }
 
 template <typename T, bool IMP>
@@ -627,8 +678,11 @@ template <typename T>
 cudaError_t set_smem_attributes()
 {
     const int big = (int)SMEM_MAX;
-    cudaError_t e = cudaFuncSetAttribute(k1_cells<T, K1_TX<T>, K1_TY<T>, K1_G<T>, K1_S<T>>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k1_smem_of<T>());
+    cudaError_t e = cudaFuncSetAttribute(k1_kernel<T, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)k1_smem_of<T>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k1_kernel<T, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)k1_smem_of<T>());
     auto set = [&](auto k) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     };
@@ -659,7 +713,7 @@ void enqueue_iteration(Impl<T>& im, int ncases, cudaStream_t s, cudaEvent_t* ev 
         }
         Batch<T> b{im.d_cases, ncases, im.d_off + (size_t)sp.table * stride};
         switch (sp.kind) {
-            case 0: launch_k1<T>(sp.total, sp.smem, b, s); break;
+            case 0: launch_k1<T>(sp.shape, sp.total, sp.smem, b, s); break;
             case 1: k2_face_params<T><<<sp.total, 128, 0, s>>>(b); break;
             case 2: k3_macro<T><<<sp.total, K3_THREADS, 0, s>>>(b); break;
             case 3: k_tables<T><<<sp.total, 128, 0, s>>>(b); break;
@@ -710,6 +764,33 @@ hbugks_status capture(hbugks_t h, Impl<T>& im)
         cudaGraphDestroy(g);
         (which == 0 ? h->g1 : h->gN) = ex;
     }
+    // The pseudo-time loop on the device: a graph holding one conditional while node, whose body is one
+    // iteration followed by the loop test; one launch runs up to the requested number of iterations and stops
+    // by itself once every case has converged (or diverged, or a wait failed), with no host round trip.
+    cudaGraph_t g;
+    HB_CK(cudaGraphCreate(&g, 0));
+    struct GraphGuard {
+        cudaGraph_t g;
+        ~GraphGuard() { cudaGraphDestroy(g); }
+    } guard{g};
+    cudaGraphConditionalHandle hc;
+    HB_CK(cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault));
+    // the parameter struct holds a union of non-trivial members: zeroed raw storage stands in for a constructor
+    alignas(cudaGraphNodeParams) unsigned char np_raw[sizeof(cudaGraphNodeParams)];
+    memset(np_raw, 0, sizeof np_raw);
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_raw);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hc;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    HB_CK(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    HB_CK(cudaStreamBeginCaptureToGraph(h->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    enqueue_iteration(im, h->ncases, h->s);
+    k_loop_test<<<1, 32, 0, h->s>>>(hc, im.d_loop, im.d_status, h->ncases, im.d_err);
+    HB_CK(cudaStreamEndCapture(h->s, &body));
+    HB_CK(cudaGraphInstantiate(&h->gW, g, 0));
     return HBUGKS_OK;
 }
 
@@ -856,6 +937,20 @@ auto dispatch(hbugks_t h, F&& fn) -> decltype(fn(*h->d))
         if (h->f) return fn(*h->f);
         return fn(*h->d);
     }
+}
+
+}  // namespace
+
+namespace {
+
+// up to n iterations in one launch of the device-side loop (stream-ordered: the count is set on the stream)
+template <typename T>
+hbugks_status launch_loop(hbugks_t h, Impl<T>& im, int n)
+{
+    if (n <= 0) return HBUGKS_OK;
+    k_set_int<<<1, 1, 0, h->s>>>(im.d_loop, n);
+    HB_CK(cudaGraphLaunch(h->gW, h->s));
+    return HBUGKS_OK;
 }
 
 }  // namespace
@@ -1014,6 +1109,7 @@ void hbugks_destroy(hbugks_t h)
     if (h->s) cudaStreamSynchronize(h->s);
     if (h->g1) cudaGraphExecDestroy(h->g1);
     if (h->gN) cudaGraphExecDestroy(h->gN);
+    if (h->gW) cudaGraphExecDestroy(h->gW);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->s) cudaStreamDestroy(h->s);
@@ -1140,6 +1236,7 @@ static hbugks_status launch_iters(hbugks_t h, int n)
     return HBUGKS_OK;
 }
 
+
 hbugks_status hbugks_enqueue_iterations(hbugks_t h, int n)
 {
     if (!h || n < 0) return HBUGKS_EINVAL;
@@ -1148,7 +1245,7 @@ hbugks_status hbugks_enqueue_iterations(hbugks_t h, int n)
         if (rc) return rc;
         HB_CK(cudaMemsetAsync(im.d_tol, 0, sizeof(double), h->s));
         k_begin_call<<<(h->ncases + 127) / 128, 128, 0, h->s>>>(im.d_status, h->ncases);
-        if ((rc = launch_iters(h, n))) return rc;
+        if ((rc = h->loop_mode == 0 ? launch_loop(h, im, n) : launch_iters(h, n))) return rc;
         return end(h);
     });
 }
@@ -1173,17 +1270,23 @@ hbugks_status hbugks_iterate(hbugks_t h, int max_iters, double tol_rho, int* ite
             return HBUGKS_OK;
         };
         int err = 0;
-        while (done < max_iters) {
-            int n = std::min(CHUNK, max_iters - done);
-            if ((rc = launch_iters(h, n))) return rc;
-            done += n;
-            if ((rc = poll(err))) return rc;
-            if (err) break;
-            bool any = false;
-            for (int k = 0; k < h->ncases; ++k) any = any || st[k].active;
-            if (!any) break;
+        if (h->loop_mode == 0) {
+            // one launch of the device-side loop, one read of the statuses at its end
+            if ((rc = launch_loop(h, im, max_iters))) return rc;
+            done = max_iters;
+        } else {
+            while (done < max_iters) {
+                int n = std::min(CHUNK, max_iters - done);
+                if ((rc = launch_iters(h, n))) return rc;
+                done += n;
+                if ((rc = poll(err))) return rc;
+                if (err) break;
+                bool any = false;
+                for (int k = 0; k < h->ncases; ++k) any = any || st[k].active;
+                if (!any) break;
+            }
         }
-        if (done == 0 && (rc = poll(err))) return rc;
+        if ((h->loop_mode == 0 || done == 0) && (rc = poll(err))) return rc;
         if (err) {
             // the state is the one before the failed iteration (its residual kernel did not run, so the state
             // buffers did not swap); clear the error word and the test hook, and recompute the local steps of
@@ -1325,6 +1428,43 @@ hbugks_status hbugks_harmonic_noalloc(int nx, int ny, int nu, int nv, const doub
     return HBUGKS_OK;
 }
 
+hbugks_status hbugks_copy_state(hbugks_t dst, int dst_case, hbugks_t src, int src_case)
+{
+    if (!dst || !src || dst == src || dst_case < 0 || dst_case >= dst->ncases || src_case < 0 ||
+        src_case >= src->ncases)
+        return HBUGKS_EINVAL;
+    return dispatch(src, [&](auto& is) -> hbugks_status {
+        return dispatch(dst, [&](auto& id) -> hbugks_status {
+            const HostCase& hs = is.hc[src_case];
+            const HostCase& hd = id.hc[dst_case];
+            if (hs.nx != hd.nx || hs.ny != hd.ny || hs.nu != hd.nu || hs.nv != hd.nv || hs.nt != hd.nt ||
+                hs.nvp != hd.nvp || hs.xn != hd.xn || hs.yn != hd.yn || hs.u != hd.u || hs.v != hd.v ||
+                hs.wu != hd.wu || hs.wv != hd.wv)
+                return HBUGKS_EINVAL;
+            const auto& ds = is.dc[src_case];
+            const auto& dd = id.dc[dst_case];
+            // everything enqueued on src so far, then the current buffer of the source case
+            hbugks_status rc = begin(src);
+            if (rc) return rc;
+            CaseStatus st;
+            HB_CK(cudaMemcpyAsync(&st, is.d_status + src_case, sizeof st, cudaMemcpyDeviceToHost, src->s));
+            HB_CK(cudaStreamSynchronize(src->s));
+            if ((rc = end(src))) return rc;
+            if ((rc = begin(dst))) return rc;
+            const size_t n = (size_t)hd.nvb * hd.nc * hd.nt * VB;
+            using TS = std::remove_const_t<typename std::remove_pointer<decltype(ds.tu)>::type>;
+            using TD = std::remove_const_t<typename std::remove_pointer<decltype(dd.tu)>::type>;
+            k_status_reset<<<(dst->ncases + 127) / 128, 128, 0, dst->s>>>(id.d_status, dst->ncases, dst_case, -1);
+            k_convert_state<TS, TD><<<(unsigned)((n + 255) / 256), 256, 0, dst->s>>>(ds.f[st.parity], dd.f[0], n);
+            HB_CK(cudaMemcpyAsync(dd.W[0], ds.W[st.parity], sizeof(double) * hd.nt * hd.nc * 4,
+                                  cudaMemcpyDeviceToDevice, dst->s));
+            enqueue_steps(id, dst->ncases, dst->s);
+            HB_CK(cudaStreamSynchronize(dst->s));
+            return end(dst);
+        });
+    });
+}
+
 hbugks_status hbugks_test_expire_wait(hbugks_t h)
 {
     if (!h) return HBUGKS_EINVAL;
@@ -1366,6 +1506,7 @@ hbugks_status hbugks_set_tile_shape(hbugks_t h, int case_index, int tx, int ty)
         HB_CK(cudaStreamSynchronize(h->s));
         if (h->g1) { cudaGraphExecDestroy(h->g1); h->g1 = nullptr; }
         if (h->gN) { cudaGraphExecDestroy(h->gN); h->gN = nullptr; }
+        if (h->gW) { cudaGraphExecDestroy(h->gW); h->gW = nullptr; }
         if ((rc = capture(h, im)) != HBUGKS_OK) return rc;
         return end(h);
     });
@@ -1375,11 +1516,18 @@ int hbugks_launches_per_iteration(hbugks_t h)
 {
     if (!h) return -1;
     return dispatch(h, [&](auto& im) -> int {
-        int n = 1;   // residual kernel
+        int n = h->loop_mode == 0 ? 2 : 1;   // residual kernel (and the loop test of the device-side loop)
         for (auto& sp : im.specs)
             if (sp.kind != 5 && sp.total) ++n;
         return n;
     });
+}
+
+hbugks_status hbugks_set_loop_mode(hbugks_t h, int mode)
+{
+    if (!h || (mode != 0 && mode != 1)) return HBUGKS_EINVAL;
+    h->loop_mode = mode;
+    return HBUGKS_OK;
 }
 
 const char* hbugks_status_string(hbugks_status s)

@@ -11,73 +11,67 @@
 //              the semi-implicit collision update (Eq. fv_h).
 // A CTA of k1_cells owns a tile of cells and one level and runs over all velocity blocks; a CTA of k4_cells
 // owns a tile of cells and one velocity block and runs over all levels.  Both stage the tile and its halo in
-// shared memory with bulk copies (TMA) completing on an mbarrier.
+// shared memory with bulk copies (TMA) completing on an mbarrier.  The distributions h and b of a velocity are
+// stored side by side and carried as one pair (hb_common.cuh): one 8-byte access and, in single precision, one
+// packed FP32x2 instruction for both wherever they see the same arithmetic (differences, limited slopes,
+// reconstruction, the flux combination, spectral source and update).
 #pragma once
 #include "hb_common.cuh"
 
 namespace hb {
 
-template <typename T>
-__device__ __forceinline__ T vleer(T s1, T s2);
-template <>
-__device__ __forceinline__ double vleer<double>(double s1, double s2)
+// van Leer limiter of a pair: 2 s1 s2 / (s1 + s2) where s1 s2 > 0, else 0.  Single precision: the limited slope
+// needs no correctly rounded division (approximate reciprocal, 2 ulp)
+__device__ __forceinline__ float rcp_approx(float x)
 {
-    double p = s1 * s2;
-    return p > 0.0 ? (p + p) / (s1 + s2) : 0.0;
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
-// single precision: the limited slope needs no correctly rounded division (2-ulp reciprocal form)
-template <>
-__device__ __forceinline__ float vleer<float>(float s1, float s2)
+__device__ __forceinline__ float2 vleer2(float2 s1, float2 s2)
 {
-    float p = s1 * s2;
-    return p > 0.f ? __fdividef(p + p, s1 + s2) : 0.f;
+    const float2 p = pmul(s1, s2);
+    const float2 den = padd(s1, s2);
+    const float2 q = pmul(padd(p, p), make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+    return make_float2(p.x > 0.f ? q.x : 0.f, p.y > 0.f ? q.y : 0.f);
+}
+__device__ __forceinline__ double2 vleer2(double2 s1, double2 s2)
+{
+    const double px = s1.x * s2.x, py = s1.y * s2.y;
+    return make_double2(px > 0.0 ? (px + px) / (s1.x + s2.x) : 0.0, py > 0.0 ? (py + py) / (s1.y + s2.y) : 0.0);
 }
 
-// van Leer slope of a cell from its two neighbours along one axis; a missing neighbour (wall) makes the
-// available one-sided difference the slope, a single cell along the axis has none
-template <typename T>
-__device__ __forceinline__ T slope(T fm, T f0, T fp, T wm, T wp, bool has_m, bool has_p, bool several)
+// Limited slope of (h, b) of a cell from its two neighbours along one axis, wm = 1/(x_i - x_{i-1}),
+// wp = 1/(x_{i+1} - x_i) (non-uniform spacing); a missing neighbour (wall) makes the available one-sided
+// difference the slope, a single cell along the axis has none
+template <typename V, typename T>
+__device__ __forceinline__ V slope2(V fm, V f0, V fp, T wm, T wp, bool has_m, bool has_p, bool several)
 {
-    T s1 = (f0 - fm) * wm, s2 = (fp - f0) * wp;
+    V s1 = pmul(psub(f0, fm), bc(wm)), s2 = pmul(psub(fp, f0), bc(wp));
     if (!has_m) s1 = s2;
     if (!has_p) s2 = s1;
-    return several ? vleer(s1, s2) : T(0);
+    return several ? vleer2(s1, s2) : bc(T(0));
+}
+// both neighbours present
+template <typename V, typename T>
+__device__ __forceinline__ V slope2i(V fm, V f0, V fp, T wm, T wp)
+{
+    return vleer2(pmul(psub(f0, fm), bc(wm)), pmul(psub(fp, f0), bc(wp)));
 }
 
-// 16-byte read-only vector loads of N consecutive parameters (N a multiple of 16 / sizeof(T), p 16-byte aligned)
-template <int N>
-__device__ __forceinline__ void ldv(const float* p, float* o)
+// spectral source of one cell and lane: sum_d e_d (f_{n-d} - f_{n+d}) for (h, b) (Eq. D_explicit in paired
+// form), levels lv pairs apart in shared memory, e_d as broadcast pairs (etb[0] = 0)
+template <int NH, typename V>
+__device__ __forceinline__ V spectral2(const V* fc, int n, int nt, int lv, const V* etb)
 {
-#pragma unroll
-    for (int k = 0; k < N; k += 4) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(p + k));
-        o[k] = v.x; o[k + 1] = v.y; o[k + 2] = v.z; o[k + 3] = v.w;
-    }
-}
-template <int N>
-__device__ __forceinline__ void ldv(const double* p, double* o)
-{
-#pragma unroll
-    for (int k = 0; k < N; k += 2) {
-        const double2 v = __ldg(reinterpret_cast<const double2*>(p + k));
-        o[k] = v.x; o[k + 1] = v.y;
-    }
-}
-
-// spectral source of one cell and lane: sum_d e_d (f_{n-d} - f_{n+d}) for h and b (Eq. D_explicit in paired
-// form), levels lv elements apart in shared memory
-template <int NH, typename T>
-__device__ __forceinline__ void spectral(const T* hc, const T* bc, int n, int nt, int lv, const T* et, T& eh, T& eb)
-{
-    eh = T(0);
-    eb = T(0);
+    V e = etb[0];
 #pragma unroll
     for (int d = 1; d <= NH; ++d) {
         int nm = n - d; nm += nm < 0 ? nt : 0;
         int np = n + d; np -= np >= nt ? nt : 0;
-        eh += et[d] * (hc[nm * lv] - hc[np * lv]);
-        eb += et[d] * (bc[nm * lv] - bc[np * lv]);
+        e = pfma(etb[d], psub(fc[nm * lv], fc[np * lv]), e);
     }
+    return e;
 }
 
 __device__ __forceinline__ void mbar_setup(uint64_t* bars, int n)
@@ -124,9 +118,14 @@ __device__ __forceinline__ T lane_totals(T (&v)[N], int lane)
 // A wall face takes 0..12 and 18..22 from the velocities moving into the wall only and 13..17 from all.
 // Half-face slots per (cell, level): 0 x-face of the u > 0 class (the right face), 1 u < 0 (left face),
 // 2 v > 0 (top face), 3 v < 0 (bottom face).
-template <typename T, int TX, int TY, int G, int S>
+// With SEP the case's velocity grid has no zero node and each sign class has 1, 2, 4, 8, 16 or 32 u-nodes, so a
+// lane sees the same u in every block of a class (blocks hold whole rows of the class, u fastest): every sum
+// w u^a v^b d factors into w_u u^a (the lane's) times sum over the lane's velocities of w_v v^b d, and the lane
+// keeps only those v-moments (34 sums instead of 59), multiplying by w_u u^a when the class changes.
+template <typename T, int TX, int TY, int G, int S, bool SEP>
 __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
 {
+    using V = P2<T>;
     constexpr int PX = TX + 2, PY = TY + 2, NR = PX * PY, NWC = TX * TY;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bars[S], empty[S];
@@ -151,32 +150,31 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
         for (int k = 0; k < S; ++k) mbar_init(empty + k, NWC);   // one arrival per warp: slot read
     }
     mbar_setup(bars, S);
-    // staged rectangle: columns i0-1 .. i0+TX, rows j0-1 .. j0+TY; S buffers [G][h, b][NR][32] in a ring
+    // staged rectangle: columns i0-1 .. i0+TX, rows j0-1 .. j0+TY; S buffers [G][NR][32] of (h, b) pairs
     constexpr size_t blk = (size_t)NR * VB;
-    T* buf = reinterpret_cast<T*>(smem_raw);
+    V* buf = reinterpret_cast<V*>(smem_raw);
     const int p = cd.st->parity;
-    const T* gh = cd.dh[p];
-    const T* gb = cd.db[p];
+    const V* gf = cd.f[p];
     const int c0 = max(i0 - 1, 0), c1 = min(i0 + TX + 1, nx);
+    const uint32_t row_b = (uint32_t)((c1 - c0) * VB * sizeof(V));
     uint32_t rbytes = 0;
     for (int r = 0; r < PY; ++r) {
         const int jj = j0 - 1 + r;
-        if (jj >= 0 && jj < ny) rbytes += (uint32_t)((c1 - c0) * VB * sizeof(T));
+        if (jj >= 0 && jj < ny) rbytes += row_b;
     }
     const int nchunk = (nvb + G - 1) / G;
     int* err = cd.err;
     auto issue = [&](int k) {
         const int vb0 = k * G, gk = min(G, nvb - vb0);
-        T* dst = buf + (size_t)(k % S) * G * 2 * blk;
-        if (lane == 0) mbar_arrive_expect(&bars[k % S], (uint32_t)(2 * gk) * rbytes);
+        V* dst = buf + (size_t)(k % S) * G * blk;
+        if (lane == 0) mbar_arrive_expect(&bars[k % S], (uint32_t)gk * rbytes);
         __syncwarp();
-        for (int q = lane; q < gk * 2 * PY; q += 32) {
-            const int r = q % PY, ga = q / PY;   // ga = 2 g + array
+        for (int q = lane; q < gk * PY; q += 32) {
+            const int r = q % PY, g = q / PY;
             const int jj = j0 - 1 + r;
             if (jj < 0 || jj >= ny) continue;
-            const size_t src = ((size_t)(vb0 + (ga >> 1)) * nt + n) * nc * VB + ((size_t)jj * nx + c0) * VB;
-            bulk_g2s(dst + (size_t)ga * blk + (size_t)(r * PX + c0 - (i0 - 1)) * VB, ((ga & 1) ? gb : gh) + src,
-                     (uint32_t)((c1 - c0) * VB * sizeof(T)), &bars[k % S]);
+            const size_t src = ((size_t)(vb0 + g) * nt + n) * nc * VB + ((size_t)jj * nx + c0) * VB;
+            bulk_g2s(dst + (size_t)g * blk + (size_t)(r * PX + c0 - (i0 - 1)) * VB, gf + src, row_b, &bars[k % S]);
         }
     };
     if (warp == 0)
@@ -194,28 +192,63 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
     const T wxm = valid && hm ? T(cd.rdx[i - 1]) : T(0), wxp = valid && hp ? T(cd.rdx[i]) : T(0);
     const T wym = valid && vm ? T(cd.rdy[j - 1]) : T(0), wyp = valid && vp ? T(cd.rdy[j]) : T(0);
     const T hxh = valid ? T(cd.hx[i]) : T(0), hyh = valid ? T(cd.hy[j]) : T(0);
+    const bool inner = hm && hp && vm && vp;                 // every neighbour present: no wall branches
     const int kc = (tj + 1) * PX + ti + 1;
     const T* __restrict__ tu = cd.tu;
     const T* __restrict__ tv = cd.tv;
-    const T* __restrict__ tw = cd.tw;
+    const T* __restrict__ tw = SEP ? cd.twv : cd.tw;       // SEP: the v-factor w_v of each weight
     const int* __restrict__ vcls = cd.vcls;
 
-    T ax[NM], ay[NM], ac[NCM];
+    // general: the 23 + 23 + 13 sums per lane; SEP: v-moments per lane (x-face h: 4, b: 2, tangential h: 3,
+    // b: 1, normal-flux h: 3, b: 1; the y-face alike; cell h: 4, b: 2), folded into the 23 + 23 + 13 at a
+    // class change
+    constexpr int NA = SEP ? 14 : NM, NC = SEP ? 6 : NCM;
+    T ax[NA], ay[NA], cc[NC], ac[NCM];
 #pragma unroll
-    for (int q = 0; q < NM; ++q) { ax[q] = T(0); ay[q] = T(0); }
+    for (int q = 0; q < NA; ++q) { ax[q] = T(0); ay[q] = T(0); }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) cc[q] = T(0);
 #pragma unroll
     for (int q = 0; q < NCM; ++q) ac[q] = T(0);
     int cur = -1;
+    T ul = T(0), wul = T(0);                                 // SEP: the lane's u and w_u in the current class
+    // the 23 face sums of one face from its v-moments m (SEP)
+    auto unfold = [&](const T (&m)[14], T (&o)[NM]) {
+        const T w1 = wul, w2 = w1 * ul, w3 = w2 * ul, w4 = w3 * ul;     // w_u u^a
+        o[0] = w1 * m[0]; o[1] = w2 * m[0]; o[2] = w1 * m[1]; o[3] = w3 * m[0]; o[4] = w2 * m[1];
+        o[5] = w1 * m[2]; o[6] = w4 * m[0]; o[7] = w3 * m[1]; o[8] = w2 * m[2]; o[9] = w1 * m[3];
+        o[10] = w1 * m[4]; o[11] = w2 * m[4]; o[12] = w1 * m[5];
+        o[13] = w1 * m[6]; o[14] = w2 * m[6]; o[15] = w1 * m[7]; o[16] = w3 * m[6] + w1 * m[8];
+        o[17] = w1 * m[9];
+        o[18] = w1 * m[10]; o[19] = w2 * m[10]; o[20] = w1 * m[11]; o[21] = w3 * m[10] + w1 * m[12];
+        o[22] = w1 * m[13];
+    };
     // add the sums of the current sign class to its two half-face slots
     auto flush = [&]() {
-        const T tx_ = lane_totals<NM>(ax, lane);
-        const T ty_ = lane_totals<NM>(ay, lane);
+        T tx_, ty_;
+        if constexpr (SEP) {
+            T ox[NM], oy[NM];
+            unfold(ax, ox);
+            unfold(ay, oy);
+            const T w1 = wul, w2 = w1 * ul, w3 = w2 * ul, w4 = w3 * ul;
+            ac[0] += w1 * cc[0]; ac[1] += w2 * cc[0]; ac[2] += w1 * cc[1]; ac[3] += w3 * cc[0];
+            ac[4] += w2 * cc[1]; ac[5] += w1 * cc[2]; ac[6] += w4 * cc[0]; ac[7] += w3 * cc[1];
+            ac[8] += w2 * cc[2]; ac[9] += w1 * cc[3];
+            ac[10] += w1 * cc[4]; ac[11] += w2 * cc[4]; ac[12] += w1 * cc[5];
+#pragma unroll
+            for (int q = 0; q < NC; ++q) cc[q] = T(0);
+            tx_ = lane_totals<NM>(ox, lane);
+            ty_ = lane_totals<NM>(oy, lane);
+        } else {
+            tx_ = lane_totals<NM>(ax, lane);
+            ty_ = lane_totals<NM>(ay, lane);
+        }
         if (lane < NM) {
             sacc[warp][(cur & 1) ? 1 : 0][lane] += tx_;
             sacc[warp][(cur & 2) ? 3 : 2][lane] += ty_;
         }
 #pragma unroll
-        for (int q = 0; q < NM; ++q) { ax[q] = T(0); ay[q] = T(0); }
+        for (int q = 0; q < NA; ++q) { ax[q] = T(0); ay[q] = T(0); }
     };
 
     // Ring of S slots: chunk k lands in slot k % S (mbarrier bars); each warp arrives on empty once it has
@@ -235,7 +268,7 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
             give_up(k);
             return;
         }
-        const T* cb = buf + (size_t)(k % S) * G * 2 * blk;
+        const V* cb = buf + (size_t)(k % S) * G * blk;
         const int vb0 = k * G, gk = min(G, nvb - vb0);
         if (valid) {
             // the velocities of block g + 1 are loaded while block g is summed
@@ -252,43 +285,71 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
                 if (cls != cur) {
                     if (cur >= 0) flush();
                     cur = cls;
+                    if (SEP) {
+                        ul = u;
+                        wul = __ldg(cd.twu + (vb0 + g) * VB + lane);
+                    }
                 }
-                const T* ph = cb + (size_t)(2 * g) * blk + (size_t)kc * VB + lane;
-                const T* pb = ph + blk;
-                const T f0 = ph[0], g0 = pb[0];
-                const T sxh = slope(ph[-VB], f0, ph[VB], wxm, wxp, hm, hp, sx);
-                const T syh = slope(ph[-PX * VB], f0, ph[PX * VB], wym, wyp, vm, vp, sy);
-                const T sxb = slope(pb[-VB], g0, pb[VB], wxm, wxp, hm, hp, sx);
-                const T syb = slope(pb[-PX * VB], g0, pb[PX * VB], wym, wyp, vm, vp, sy);
+                const V* ph = cb + (size_t)g * blk + (size_t)kc * VB + lane;
+                const V f0 = ph[0];
+                V sxv, syv;
+                if (inner) {
+                    sxv = slope2i(ph[-VB], f0, ph[VB], wxm, wxp);
+                    syv = slope2i(ph[-PX * VB], f0, ph[PX * VB], wym, wyp);
+                } else {
+                    sxv = slope2(ph[-VB], f0, ph[VB], wxm, wxp, hm, hp, sx);
+                    syv = slope2(ph[-PX * VB], f0, ph[PX * VB], wym, wyp, vm, vp, sy);
+                }
                 const bool xn = (cls & 1) != 0, yn = (cls & 2) != 0;
-                const T offx = xn ? -hxh : hxh, offy = yn ? -hyh : hyh;
-                T d0x = f0 + sxh * offx, e0x = g0 + sxb * offx;
-                T d0y = f0 + syh * offy, e0y = g0 + syb * offy;
-                // a velocity parallel to a wall carries nothing into it
-                if ((xn ? !hm : !hp) && u == T(0)) { d0x = T(0); e0x = T(0); }
-                if ((yn ? !vm : !vp) && v == T(0)) { d0y = T(0); e0y = T(0); }
-                const T wu = w * u, wv = w * v, wuu = wu * u, wuv = wu * v, wvv = wv * v;
-                const T m[10] = {w, wu, wv, wuu, wuv, wvv, wuu * u, wuu * v, wvv * u, wvv * v};
-                const T wq = wuu + wvv;
-#pragma unroll
-                for (int q = 0; q < 10; ++q) {
-                    ax[q] += d0x * m[q];
-                    ay[q] += d0y * m[q];
-                    ac[q] += f0 * m[q];
+                V dx = pfma(sxv, bc(xn ? -hxh : hxh), f0);       // reconstruction at the downwind x-face
+                V dy = pfma(syv, bc(yn ? -hyh : hyh), f0);
+                if (!inner) {
+                    // a velocity parallel to a wall carries nothing into it
+                    if ((xn ? !hm : !hp) && u == T(0)) dx = bc(T(0));
+                    if ((yn ? !vm : !vp) && v == T(0)) dy = bc(T(0));
                 }
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    ax[10 + q] += e0x * m[q];
-                    ay[10 + q] += e0y * m[q];
-                    ac[10 + q] += g0 * m[q];
+                const T sxh = sxv.x, sxb = sxv.y, syh = syv.x, syb = syv.y;
+                if constexpr (SEP) {
+                    // w is w_v here; v-moments of every summand
+                    const T c1 = w * v, c2 = c1 * v, c3 = c2 * v;
+                    const T txh = ul * (ul * sxh + v * syh), tyh = v * (v * syh + ul * sxh);
+                    const T txb = ul * (ul * sxb + v * syb), tyb = v * (v * syb + ul * sxb);
+                    ax[0] += dx.x * w; ax[1] += dx.x * c1; ax[2] += dx.x * c2; ax[3] += dx.x * c3;
+                    ay[0] += dy.x * w; ay[1] += dy.x * c1; ay[2] += dy.x * c2; ay[3] += dy.x * c3;
+                    ax[4] += dx.y * w; ax[5] += dx.y * c1;
+                    ay[4] += dy.y * w; ay[5] += dy.y * c1;
+                    ax[6] += syh * w; ax[7] += syh * c1; ax[8] += syh * c2; ax[9] += syb * w;
+                    ay[6] += sxh * w; ay[7] += sxh * c1; ay[8] += sxh * c2; ay[9] += sxb * w;
+                    ax[10] += txh * w; ax[11] += txh * c1; ax[12] += txh * c2; ax[13] += txb * w;
+                    ay[10] += tyh * w; ay[11] += tyh * c1; ay[12] += tyh * c2; ay[13] += tyb * w;
+                    cc[0] += f0.x * w; cc[1] += f0.x * c1; cc[2] += f0.x * c2; cc[3] += f0.x * c3;
+                    cc[4] += f0.y * w; cc[5] += f0.y * c1;
+                    continue;
                 }
-                ax[13] += syh * w; ax[14] += syh * wu; ax[15] += syh * wv; ax[16] += syh * wq; ax[17] += syb * w;
-                ay[13] += sxh * w; ay[14] += sxh * wu; ay[15] += sxh * wv; ay[16] += sxh * wq; ay[17] += sxb * w;
-                const T txh = u * (u * sxh + v * syh), tyh = v * (v * syh + u * sxh);
-                ax[18] += txh * w; ax[19] += txh * wu; ax[20] += txh * wv; ax[21] += txh * wq;
-                ay[18] += tyh * w; ay[19] += tyh * wu; ay[20] += tyh * wv; ay[21] += tyh * wq;
-                ax[22] += u * (u * sxb + v * syb) * w;
-                ay[22] += v * (v * syb + u * sxb) * w;
+                if constexpr (!SEP) {
+                    const T wu = w * u, wv = w * v, wuu = wu * u, wuv = wu * v, wvv = wv * v;
+                    const T m[10] = {w, wu, wv, wuu, wuv, wvv, wuu * u, wuu * v, wvv * u, wvv * v};
+                    const T wq = wuu + wvv;
+#pragma unroll
+                    for (int q = 0; q < 10; ++q) {
+                        ax[q] += dx.x * m[q];
+                        ay[q] += dy.x * m[q];
+                        ac[q] += f0.x * m[q];
+                    }
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        ax[10 + q] += dx.y * m[q];
+                        ay[10 + q] += dy.y * m[q];
+                        ac[10 + q] += f0.y * m[q];
+                    }
+                    ax[13] += syh * w; ax[14] += syh * wu; ax[15] += syh * wv; ax[16] += syh * wq; ax[17] += syb * w;
+                    ay[13] += sxh * w; ay[14] += sxh * wu; ay[15] += sxh * wv; ay[16] += sxh * wq; ay[17] += sxb * w;
+                    const T txh = u * (u * sxh + v * syh), tyh = v * (v * syh + u * sxh);
+                    ax[18] += txh * w; ax[19] += txh * wu; ax[20] += txh * wv; ax[21] += txh * wq;
+                    ay[18] += tyh * w; ay[19] += tyh * wu; ay[20] += tyh * wv; ay[21] += tyh * wq;
+                    ax[22] += u * (u * sxb + v * syb) * w;
+                    ay[22] += v * (v * syb + u * sxb) * w;
+                }
             }
         }
         __syncwarp();
@@ -307,67 +368,113 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
 template <typename T, int TX, int TY, int G, int S>
 constexpr size_t k1_cells_smem()
 {
-    return (size_t)S * G * 2 * (TX + 2) * (TY + 2) * VB * sizeof(T);
+    return (size_t)S * G * (TX + 2) * (TY + 2) * VB * sizeof(P2<T>);
 }
 
 // ------------------------------------------------------------------------------ K4: micro update
 
-// Micro flux (delta form, divided by dG_f) through the downwind face of the reconstructing cell, for one lane:
-// u_n [C1' dH + H Q + C4' d0 + C5' (u_n s_n + u_t s_t)] and the b counterpart, from the face's parameters fp
-// (shared memory; the cubic at qo and linear term at lo belong to the upwind side) and the expm1 factors
-// (ex, ey) of the interface Maxwellian at the lane's velocity.
-template <typename T>
-__device__ __forceinline__ void flux_down(const T* fp, int qo, int lo, T ex, T ey, T href, T u, T v, T un, T ut, T d0,
-                                          T e0, T sn, T st, T snb, T stb, T& Hf, T& Bf)
+// Micro flux pair (delta form, divided by dG_f) through the downwind face of the reconstructing cell, for one
+// lane: u_n [C1' dH + H Q + C4' d0 + C5' (u_n s_n + u_t s_t)] for h and u_n [C1' dB + B (Q + lin) + C4' e0 +
+// C5' (...)] for b, from the face's parameters fp (shared memory; the cubic at qo and linear term at lo belong to
+// the upwind side), the expm1 factors (ex, ey) of the interface Maxwellian at the lane's velocity, the
+// reconstructed pair d0 and the normal and tangential slope pairs; hb, unb, utb are (H_ref, H_ref), (u_n, u_n)
+// and (u_t, u_t).  With g = (r - 1) + r (ex + ey + ex ey), dH = H_ref g and H = H_ref (1 + g), so the Maxwellian
+// part is H_ref [Q + g (C1' + Q)] for h and H_ref [i2l (Qb + g (C1' + Qb)) + C1' (i2l - i2l0)] for b.
+template <typename T, typename V>
+__device__ __forceinline__ V flux2(const T* fp, int qo, int lo, T ex, T ey, T u, T v, V hb, V unb, V utb, V d0,
+                                   V sn, V st)
 {
-    const T* sc = fp + F_RM1;      // r - 1, r, 1/(2 lam), 1/(2 lam) - 1/(2 lam0), C1', C4', C5', nin
-    const T E = ex + ey + ex * ey;
-    const T dH = href * (sc[0] + sc[1] * E);
-    const T H = href + dH;
-    const T i2l = sc[2];
-    const T dB = dH * i2l + href * sc[3];
+    const T* sc = fp + F_RM1;      // r - 1, r, 1/(2 lam), 1/(2 lam) - 1/(2 lam0), C1', C4', C5', C1' (..)
+    const T g = sc[0] + sc[1] * (ex + ey + ex * ey);
     const T* l = fp + lo;
     const T Q = cubic(fp + qo, u, v);
     const T Qb = Q + l[0] + l[1] * u + l[2] * v;
-    Hf = un * (sc[4] * dH + H * Q + sc[5] * d0 + sc[6] * (un * sn + ut * st));
-    Bf = un * (sc[4] * dB + H * i2l * Qb + sc[5] * e0 + sc[6] * (un * snb + ut * stb));
-    if (un == T(0)) { Hf = T(0); Bf = T(0); }
+    V m = pmul(hb, pk(Q + g * (sc[4] + Q), sc[2] * (Qb + g * (sc[4] + Qb)) + sc[7]));
+    m = pfma(bc(sc[5]), d0, m);
+    m = pfma(bc(sc[6]), pfma(unb, sn, pmul(utb, st)), m);
+    return pmul(unb, m);
 }
 
-// Flux (delta form, divided by dG_f) of the distribution a diffuse wall re-emits, rho_w H_w u_n: velocities of
-// the block leave the wall.
-template <typename T>
-__device__ __forceinline__ void flux_wall(const T* fp, const T* __restrict__ tb, int iu, int ivn, T href, T un, T& Hf,
-                                          T& Bf)
+// Flux pair (delta form, divided by dG_f) of the distribution a diffuse wall re-emits, rho_w H_w u_n: velocities
+// of the block leave the wall.
+template <typename T, typename V>
+__device__ __forceinline__ V flux_wall2(const T* fp, const T* __restrict__ tb, int iu, int ivn, T href, V unb)
 {
     const T* wp = fp + F_WRM1;
     const T ex = __ldg(tb + iu), ey = __ldg(tb + ivn);
     const T E = ex + ey + ex * ey;
     const T dHw = href * (wp[0] + wp[1] * E);
-    Hf = un * dHw;
-    Bf = un * (dHw * wp[2] + href * wp[3]);
+    return pmul(unb, pk(dHw, dHw * wp[2] + href * wp[3]));
 }
 
-// Shared-memory layout of k4_cells (element offsets in T, each block 16-byte aligned):
-//   own   [nt][h, b][NCT][32]      the tile's own cells on every level (spectral source, h^k of the update)
-//   rect  [2][h, b][NR][32]        per level: the tile with its halo, (TX+3) x (TY+3) cells, two cells on the
+// Equilibrium pair (H+ - H_ref, B+ - B_ref) of one cell-parameter slot q at the lane's velocity: the Maxwellian
+// from the cell table factors (ex, ey), with g = (r - 1) + r (ex + ey + ex ey) so that dH = H_ref g,
+// dB = H_ref (g i2l + (i2l - i2l0)), and with the Shakhov model the correction (L Q) H for h and (L Q + 2 L) B for
+// b (L, Q the linear and quadratic factors of s (c.q)(2 lam |c|^2 - 4); r2 = u^2 + v^2; hb = (H_ref, H_ref)).
+template <typename T>
+__device__ __forceinline__ P2<T> eq2(const T* q, T ex, T ey, P2<T> hb, T u, T v, T r2, bool shakhov)
+{
+    const T g = q[E_RM1] + q[E_R] * (ex + ey + ex * ey);
+    const T i2l = q[E_I2L];
+    const P2<T> m = pk(g, g * i2l + q[E_DI2L]);
+    if (!shakhov) return pmul(hb, m);
+    const T L = q[E_L] + q[E_L + 1] * u + q[E_L + 2] * v;
+    const T Qs = q[E_Q] + q[E_Q + 1] * u + q[E_Q + 2] * v + q[E_Q + 3] * r2;
+    const T sk = L * Qs;
+    return pmul(hb, pfma(bc(T(1) + g), pk(sk, i2l * (sk + T(2) * L)), m));
+}
+
+// First-pass work item of a k4_cells CTA (one warp): a tile cell (both downwind faces), an upwind halo cell (the
+// tile face it lies upwind of) or a wall face of the tile (the re-emitted distribution); built once per CTA.
+template <typename T>
+struct alignas(16) K4Item {
+    int kind;        // 0 none, 1 tile cell, 2 halo cell: x-face, 3 halo cell: y-face, 4 wall x-face, 5 wall y-face
+    int rect;        // offset (pairs) of the cell in a rectangle slot
+    int fx, fy;      // flux-store offsets (pairs) of the x- and y-face
+    int px, py;      // face-parameter offsets of the x- and y-face
+    int tx, ty;      // interface table offsets (face * N_T * (nu + nv)); wall items: the wall's table row index
+    int flags;       // neighbours present: 1 i-1, 2 i+1, 4 j-1, 8 j+1; 16 nx > 1, 32 ny > 1
+    int pad[3];
+    T w[6];          // 1/(x_i - x_{i-1}), 1/(x_{i+1} - x_i), the same in y, signed half widths to the faces
+};
+
+// Shared-memory layout of k4_cells (byte offsets, pairs for distributions, each block 16-byte aligned):
+//   own   [nt][NCT][32] pairs      the tile's own cells on every level (spectral source, h^k of the update)
+//   rect  [2][NR][32] pairs        per level: the tile with its halo, (TX+3) x (TY+3) cells, two cells on the
 //                                  upwind side of each axis and one on the downwind side (ring of 2 levels)
-//   fp    [2][NFT][NP]             per level: parameters of the tile's faces (ring of 2 levels)
-//   cp    [2][NCT][NCP]            per level: update coefficients of the tile's cells (ring of 2 levels)
-//   flux  [2][h, b][NFT][32]       per level: micro fluxes of the tile's faces (double buffered)
+//   fp    [2][NFT][NP] T           per level: parameters of the tile's faces (ring of 2 levels)
+//   cp    [2][NCT][NCP] T          per level: update coefficients of the tile's cells (ring of 2 levels)
+//   flux  [2][NFT][32] pairs       per level: micro fluxes of the tile's faces (double buffered)
+//   spec  [nt][nt] pairs           the spectral matrix E (Eq. D_explicit) as broadcast pairs
 template <typename T, int TX, int TY>
 struct K4Layout {
+    using V = P2<T>;
     static constexpr int PX = TX + 3, PY = TY + 3, NR = PX * PY, NCT = TX * TY;
     static constexpr int NFX = TY * (TX + 1), NFY = (TY + 1) * TX, NFT = NFX + NFY;
-    static constexpr size_t RECT = (size_t)2 * NR * VB;                 // one ring slot, h and b
-    static constexpr size_t FP = (size_t)NFT * NP, CP = (size_t)NCT * NCP, FLUX = (size_t)2 * NFT * VB;
-    __host__ __device__ static constexpr size_t own_elems(int nt) { return (size_t)nt * 2 * NCT * VB; }
-    __host__ __device__ static constexpr size_t rect_off(int nt) { return own_elems(nt); }
-    __host__ __device__ static constexpr size_t fp_off(int nt) { return rect_off(nt) + 2 * RECT; }
-    __host__ __device__ static constexpr size_t cp_off(int nt) { return fp_off(nt) + 2 * FP; }
-    __host__ __device__ static constexpr size_t flux_off(int nt) { return cp_off(nt) + 2 * CP; }
-    __host__ __device__ static constexpr size_t bytes(int nt) { return (flux_off(nt) + 2 * FLUX) * sizeof(T); }
+    static constexpr size_t RECT = (size_t)NR * VB;                     // pairs per ring slot
+    static constexpr size_t FP = (size_t)NFT * NP, CP = (size_t)NCT * NCP, FLUX = (size_t)NFT * VB;
+    __host__ __device__ static constexpr size_t own_bytes(int nt) { return (size_t)nt * NCT * VB * sizeof(V); }
+    __host__ __device__ static constexpr size_t rect_off(int nt) { return own_bytes(nt); }
+    __host__ __device__ static constexpr size_t fp_off(int nt) { return rect_off(nt) + 2 * RECT * sizeof(V); }
+    __host__ __device__ static constexpr size_t cp_off(int nt) { return fp_off(nt) + 2 * FP * sizeof(T); }
+    __host__ __device__ static constexpr size_t flux_off(int nt) { return cp_off(nt) + 2 * CP * sizeof(T); }
+    __host__ __device__ static constexpr size_t spec_off(int nt) { return flux_off(nt) + 2 * FLUX * sizeof(V); }
+    __host__ __device__ static constexpr size_t bytes(int nt) { return spec_off(nt) + (size_t)nt * nt * sizeof(V); }
 };
+
+// Spectral source of RC cells on one level n: e_c = sum_m E_nm (f_m - f_n) over the levels m of cell c's own-cell
+// store (level stride LV pairs), E's row n as broadcast pairs.  Subtracting f_n, which E maps to zero, keeps a
+// level-constant state an exact fixed point and rounds relative to the level differences.
+template <int NT, int RC, int LV, typename V>
+__device__ __forceinline__ void spectral_rows(const V* en, const V* const (&fc)[RC], const V (&fn)[RC], V (&e)[RC])
+{
+#pragma unroll
+    for (int m = 0; m < NT; ++m) {
+        const V c = en[m];
+#pragma unroll
+        for (int q = 0; q < RC; ++q) e[q] = pfma(c, psub(fc[q][m * LV], fn[q]), e[q]);
+    }
+}
 
 // A CTA: a TX x TY tile of cells, one velocity block, all levels.  Per level, the first pass reconstructs
 // every tile cell and the upwind halo cells and evaluates the flux through each one's downwind face (every
@@ -377,18 +484,20 @@ struct K4Layout {
 // leaves each level's right-hand side in the own-cell store and a last pass applies the per-cell inverse
 // across levels.  Batch k of bulk copies (the halo rectangle and face parameters of level k, the cell
 // coefficients of level k - 1; batch 0 also every level of the tile's own cells) completes on mbarrier k & 1
-// and is issued one level ahead of its use.
+// and is issued one level ahead of its use.  Every index of a warp's work items is formed once per CTA (item
+// table in shared memory); a level adds only its buffer and table offsets.
 template <typename T, int TX, int TY, int NW, bool IMP>
 __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
 {
     using L = K4Layout<T, TX, TY>;
-    constexpr int PX = L::PX, PY = L::PY, NR = L::NR, NCT = L::NCT, NFX = L::NFX, NFT = L::NFT;
-    constexpr int NIT = NCT + TY + TX, NPASS = (NIT + NW - 1) / NW;
-    constexpr int lv = NR * VB;                               // one array of one rectangle slot
+    using V = P2<T>;
+    constexpr int PX = L::PX, PY = L::PY, NCT = L::NCT, NFX = L::NFX;
+    constexpr int NIT = NCT + TY + TX, NPASS = (NIT + NW - 1) / NW, RC = (NCT + NW - 1) / NW;
     constexpr int SROWS = 4;                                  // tile rows per strip of the CTA order
+    constexpr int LVO = NCT * VB;                             // level stride of the own-cell store (pairs)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bars[2];
-    __shared__ T gxr[PX], gxh[PX], gyr[PY], gyh[PY];
+    __shared__ K4Item<T> items[NIT];
     const int cs = find_case(B.off, B.ncases, blockIdx.x);
     const CaseDev<T>& cd = B.cases[cs];
     if (!cd.st->active) return;
@@ -404,53 +513,51 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
     const int strip = tile / (ntx * SROWS), rows = min(SROWS, nty - strip * SROWS);
     const int rem = tile - strip * ntx * SROWS;
     const int i0 = (rem / rows) * TX, j0 = (strip * SROWS + rem % rows) * TY;
-    const int nt = cd.nt, nc = cd.nc, nh = cd.nh, nfx = cd.nfx, nf = cd.nf;
+    const int nt = cd.nt, nc = cd.nc, nfx = cd.nfx, nf = cd.nf;
     const int nuv = cd.nu + cd.nv;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cls = __ldg(cd.vcls + vb);
     const bool xneg = (cls & 1) != 0, yneg = (cls & 2) != 0;
     const int xlo = xneg ? -1 : -2, ylo = yneg ? -1 : -2;
     const int iend = min(i0 + TX, nx), jend = min(j0 + TY, ny);
-    T* const sm = reinterpret_cast<T*>(smem_raw);
-    T* const own = sm;
-    T* const rect = sm + L::rect_off(nt);
-    T* const fps = sm + L::fp_off(nt);
-    T* const cps = sm + L::cp_off(nt);
-    T* const fbuf = sm + L::flux_off(nt);
+    V* const own = reinterpret_cast<V*>(smem_raw);
+    V* const rect = reinterpret_cast<V*>(smem_raw + L::rect_off(nt));
+    T* const fps = reinterpret_cast<T*>(smem_raw + L::fp_off(nt));
+    T* const cps = reinterpret_cast<T*>(smem_raw + L::cp_off(nt));
+    V* const fbuf = reinterpret_cast<V*>(smem_raw + L::flux_off(nt));
+    V* const spec = reinterpret_cast<V*>(smem_raw + L::spec_off(nt));
     mbar_setup(bars, 2);
     const int p = cd.st->parity;
-    const T* gh = cd.dh[p];
-    const T* gb = cd.db[p];
+    const V* gf = cd.f[p];
     // bulk copies of the rectangle rows (clipped to the domain)
     const int c0 = max(i0 + xlo, 0), c1 = min(i0 + xlo + PX, nx);
     const int nfr = iend - i0;                                // valid cells per tile row
-    const uint32_t row_b = (uint32_t)((c1 - c0) * VB * sizeof(T));
+    const uint32_t row_b = (uint32_t)((c1 - c0) * VB * sizeof(V));
     int rrows = 0;
     for (int r = 0; r < PY; ++r) {
         const int jj = j0 + ylo + r;
         rrows += (jj >= 0 && jj < ny) ? 1 : 0;
     }
-    const uint32_t rect_b = 2u * rrows * row_b;
+    const uint32_t rect_b = (uint32_t)rrows * row_b;
     const uint32_t fp_b = (uint32_t)(((jend - j0) * (nfr + 1) + (jend - j0 + 1) * nfr) * NP * sizeof(T));
     const uint32_t cp_b = (uint32_t)((jend - j0) * nfr * NCP * sizeof(T));
     // batch k: rectangle and face parameters of level k (k < nt), cell coefficients of level k - 1 (k >= 1)
     auto issue = [&](int k) {
         const bool lvl = k < nt, cel = k >= 1;
         uint32_t bytes = (lvl ? rect_b + fp_b : 0u) + (cel ? cp_b : 0u);
-        if (k == 0) bytes += (uint32_t)(2 * nt * (jend - j0) * nfr * VB * sizeof(T));
+        if (k == 0) bytes += (uint32_t)(nt * (jend - j0) * nfr * VB * sizeof(V));
         uint64_t* bar = &bars[k & 1];
         if (lane == 0) mbar_arrive_expect(bar, bytes);
         __syncwarp();
-        const int nrect = lvl ? 2 * PY : 0, nfpr = lvl ? 2 * TY + 1 : 0, ncpr = cel ? TY : 0;
-        const int nown = k == 0 ? 2 * nt * TY : 0;
+        const int nrect = lvl ? PY : 0, nfpr = lvl ? 2 * TY + 1 : 0, ncpr = cel ? TY : 0;
+        const int nown = k == 0 ? nt * TY : 0;
         for (int q = lane; q < nrect + nfpr + ncpr + nown; q += 32) {
             if (q < nrect) {
-                const int r = q % PY, a = q / PY;
-                const int jj = j0 + ylo + r;
+                const int r = q, jj = j0 + ylo + r;
                 if (jj < 0 || jj >= ny) continue;
                 const size_t src = ((size_t)vb * nt + k) * nc * VB + ((size_t)jj * nx + c0) * VB;
-                bulk_g2s(rect + (size_t)(k & 1) * L::RECT + (size_t)a * lv + (r * PX + c0 - (i0 + xlo)) * VB,
-                         (a ? gb : gh) + src, row_b, bar);
+                bulk_g2s(rect + (size_t)(k & 1) * L::RECT + (size_t)(r * PX + c0 - (i0 + xlo)) * VB, gf + src, row_b,
+                         bar);
             } else if (q < nrect + nfpr) {
                 const int r = q - nrect;
                 if (r < TY) {                                 // x-faces of tile row r
@@ -472,45 +579,105 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
                 bulk_g2s(cps + (size_t)((k - 1) & 1) * L::CP + (size_t)r * TX * NCP,
                          cd.cpar + ((size_t)(k - 1) * nc + jj * nx + i0) * NCP, (uint32_t)(nfr * NCP * sizeof(T)), bar);
             } else {
-                const int o = q - nrect - nfpr - ncpr;        // own cells: row, array, level
-                const int r = o % TY, a = (o / TY) & 1, n = o / (2 * TY), jj = j0 + r;
+                const int o = q - nrect - nfpr - ncpr;        // own cells: row, level
+                const int r = o % TY, n = o / TY, jj = j0 + r;
                 if (jj >= ny) continue;
-                bulk_g2s(own + ((size_t)(n * 2 + a) * NCT + r * TX) * VB,
-                         (a ? gb : gh) + ((size_t)vb * nt + n) * nc * VB + ((size_t)jj * nx + i0) * VB,
-                         (uint32_t)(nfr * VB * sizeof(T)), bar);
+                bulk_g2s(own + ((size_t)n * NCT + r * TX) * VB,
+                         gf + ((size_t)vb * nt + n) * nc * VB + ((size_t)jj * nx + i0) * VB,
+                         (uint32_t)(nfr * VB * sizeof(V)), bar);
             }
         }
     };
     if (warp == 0) issue(0);
-    for (int k = threadIdx.x; k < PX; k += blockDim.x) {
-        const int ii = i0 + xlo + k;
-        gxr[k] = (ii >= 0 && ii < nx - 1) ? T(cd.rdx[ii]) : T(0);
-        gxh[k] = (ii >= 0 && ii < nx) ? T(cd.hx[ii]) : T(0);
+
+    const int NTf = nt * nuv;                                 // per-face stride of the expm1 tables
+    // ---- the first-pass items of the tile, once per CTA
+    for (int it = threadIdx.x; it < NIT; it += blockDim.x) {
+        K4Item<T> d;
+        d.kind = 0; d.rect = 0; d.fx = d.fy = d.px = d.py = d.tx = d.ty = 0; d.flags = 0;
+        d.pad[0] = d.pad[1] = d.pad[2] = 0;
+        for (int k = 0; k < 6; ++k) d.w[k] = T(0);
+        int ti, tj, kind;
+        if (it < NCT) {
+            ti = it % TX; tj = it / TX; kind = (i0 + ti < nx && j0 + tj < ny) ? 1 : 0;
+        } else if (it < NCT + TY) {
+            tj = it - NCT; ti = xneg ? iend - i0 : -1; kind = j0 + tj < ny ? 2 : 0;
+        } else {
+            ti = it - NCT - TY; tj = yneg ? jend - j0 : -1; kind = i0 + ti < nx ? 3 : 0;
+        }
+        const int i = i0 + ti, j = j0 + tj;
+        if (kind == 2 && (i < 0 || i >= nx)) {                // the tile's upwind x-face lies on a wall
+            const int fi = i < 0 ? 0 : nx;
+            kind = 4;
+            d.fx = (tj * (TX + 1) + fi - i0) * VB;
+            d.px = (tj * (TX + 1) + fi - i0) * NP;
+            d.tx = i < 0 ? 3 : 1;
+        } else if (kind == 3 && (j < 0 || j >= ny)) {
+            const int fj = j < 0 ? 0 : ny;
+            kind = 5;
+            d.fy = (NFX + (fj - j0) * TX + ti) * VB;
+            d.py = (NFX + (fj - j0) * TX + ti) * NP;
+            d.ty = j < 0 ? 0 : 2;
+        } else if (kind != 0) {
+            const int kx = ti - xlo, ky = tj - ylo;
+            const int fix = xneg ? i : i + 1, fjy = yneg ? j : j + 1;
+            const int slx = tj * (TX + 1) + fix - i0, sly = NFX + (fjy - j0) * TX + ti;
+            d.rect = (ky * PX + kx) * VB;
+            d.fx = slx * VB; d.px = slx * NP; d.tx = (j * (nx + 1) + fix) * NTf;
+            d.fy = sly * VB; d.py = sly * NP; d.ty = (nfx + fjy * nx + i) * NTf;
+            d.flags = (i > 0 ? 1 : 0) | (i < nx - 1 ? 2 : 0) | (j > 0 ? 4 : 0) | (j < ny - 1 ? 8 : 0) |
+                      (nx > 1 ? 16 : 0) | (ny > 1 ? 32 : 0);
+            d.w[0] = i > 0 ? T(cd.rdx[i - 1]) : T(0);
+            d.w[1] = i < nx - 1 ? T(cd.rdx[i]) : T(0);
+            d.w[2] = j > 0 ? T(cd.rdy[j - 1]) : T(0);
+            d.w[3] = j < ny - 1 ? T(cd.rdy[j]) : T(0);
+            d.w[4] = xneg ? -T(cd.hx[i]) : T(cd.hx[i]);
+            d.w[5] = yneg ? -T(cd.hy[j]) : T(cd.hy[j]);
+        }
+        d.kind = kind;
+        items[it] = d;
     }
-    for (int k = threadIdx.x; k < PY; k += blockDim.x) {
-        const int jj = j0 + ylo + k;
-        gyr[k] = (jj >= 0 && jj < ny - 1) ? T(cd.rdy[jj]) : T(0);
-        gyh[k] = (jj >= 0 && jj < ny) ? T(cd.hy[jj]) : T(0);
+    // ---- the spectral matrix E_nm = e_d for m = n - d, -e_d for m = n + d (levels cyclic), as broadcast pairs
+    for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) {
+        const int n = k / nt, m = k - n * nt;
+        const int d = (n - m + nt) % nt;
+        T e = T(0);
+        if (d >= 1 && d <= cd.nh) e = cd.et[d];
+        else if (d > cd.nh) e = -cd.et[nt - d];
+        spec[k] = bc(e);
     }
+
     const int av = vb * VB + lane;
     const T u = __ldg(cd.tu + av), v = __ldg(cd.tv + av), href = __ldg(cd.thref + av);
+    const T r2 = u * u + v * v;
+    const V ub = bc(u), vbb = bc(v), hb = bc(href);
     const int iu = __ldg(cd.viu + av), ivn = cd.nu + __ldg(cd.viv + av);
-    T et[8];
-#pragma unroll
-    for (int d = 0; d < 8; ++d) et[d] = cd.et[d];
     const T* __restrict__ ftab = cd.ftab;
     const T* __restrict__ wtab = cd.wtab;
     const T* __restrict__ ctab = cd.ctab;
     const bool shakhov = cd.shakhov != 0;
-    const int NTf = nt * nuv;                                 // per-face stride of the expm1 tables
     const int qoff = xneg ? F_QR : F_QL, loff = xneg ? F_LBR : F_LBL;
     const int qoffy = yneg ? F_QR : F_QL, loffy = yneg ? F_LBR : F_LBL;
     int* err = cd.err;
-
     const bool implicit = IMP && cd.spectral_implicit != 0;   // IMP = false compiles the explicit form alone
-    // a tile none of whose cells touches a wall: every stencil neighbour exists
-    const bool interior = i0 >= 1 && j0 >= 1 && i0 + TX <= nx - 1 && j0 + TY <= ny - 1;
-    constexpr bool PAIRED = NCT == 2 * NW;                    // each warp owns two tile cells in pass 1
+    // a tile none of whose first-pass cells (tile cells and upwind halo) touches a wall: every stencil neighbour
+    // of each exists
+    const bool interior = i0 >= 2 && j0 >= 2 && i0 + TX <= nx - 2 && j0 + TY <= ny - 2;
+
+    // ---- the second-pass cells of this warp: own-store, flux, coefficient and table offsets, once per CTA
+    int ofl[RC], ofb[RC], ocp[RC], oc[RC], otb[RC];
+    bool ok[RC];
+#pragma unroll
+    for (int q = 0; q < RC; ++q) {
+        const int ct = warp + q * NW, ti = ct % TX, tj = ct / TX;
+        ok[q] = ct < NCT && i0 + ti < nx && j0 + tj < ny;
+        const int c = (j0 + tj) * nx + i0 + ti;
+        ofl[q] = (tj * (TX + 1) + ti) * VB;                   // left face; the right one follows
+        ofb[q] = (NFX + tj * TX + ti) * VB;                   // bottom face; the top one is TX faces on
+        ocp[q] = ct * NCP;
+        oc[q] = ok[q] ? c : 0;
+        otb[q] = (ok[q] ? c : 0) * nt * 2 * nuv;
+    }
 
     for (int s = 0; s <= nt; ++s) {
         if (warp == 0 && s < nt) issue(s + 1);
@@ -529,233 +696,143 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
         if (s < nt) {
             // ---- pass 1, level s: reconstruction and downwind-face fluxes
             const int n = s;
-            T* Fh = fbuf + (size_t)(n & 1) * L::FLUX + lane;
-            T* Fb = Fh + NFT * VB;
-            const T* rh = rect + (size_t)(n & 1) * L::RECT + lane;
+            V* F = fbuf + (size_t)(n & 1) * L::FLUX + lane;
+            const V* rh = rect + (size_t)(n & 1) * L::RECT + lane;
             const T* fpn = fps + (size_t)(n & 1) * L::FP;
             const T* ftn = ftab + n * nuv;
-            int rfirst = 0;
-            if (PAIRED && interior) {
-                // both tile cells of the warp as one straight-line block, stores last, so that the two
-                // independent chains interleave
-                T fx[2][4];
-                int sl[2][2];
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int it = warp + q * NW, ti = it % TX, tj = it / TX;
-                    const int i = i0 + ti, j = j0 + tj;
-                    const int kx = ti - xlo, ky = tj - ylo;
-                    const int fix = xneg ? i : i + 1, fjy = yneg ? j : j + 1;
-                    sl[q][0] = tj * (TX + 1) + fix - i0;
-                    sl[q][1] = NFX + (fjy - j0) * TX + ti;
-                    const T* tbx = ftn + (j * (nx + 1) + fix) * NTf;
-                    const T* tby = ftn + (nfx + fjy * nx + i) * NTf;
-                    const T exx = __ldg(tbx + iu), eyx = __ldg(tbx + ivn);
-                    const T exy = __ldg(tby + iu), eyy = __ldg(tby + ivn);
-                    const T* ph = rh + (ky * PX + kx) * VB;
-                    const T* pb = ph + lv;
-                    const T f0 = ph[0], g0 = pb[0];
-                    const T wxm = gxr[kx - 1], wxp = gxr[kx], wym = gyr[ky - 1], wyp = gyr[ky];
-                    const T sxh = slope(ph[-VB], f0, ph[VB], wxm, wxp, true, true, true);
-                    const T sxb = slope(pb[-VB], g0, pb[VB], wxm, wxp, true, true, true);
-                    const T syh = slope(ph[-PX * VB], f0, ph[PX * VB], wym, wyp, true, true, true);
-                    const T syb = slope(pb[-PX * VB], g0, pb[PX * VB], wym, wyp, true, true, true);
-                    const T offx = xneg ? -gxh[kx] : gxh[kx], offy = yneg ? -gyh[ky] : gyh[ky];
-                    flux_down(fpn + sl[q][0] * NP, qoff, loff, exx, eyx, href, u, v, u, v, f0 + sxh * offx,
-                              g0 + sxb * offx, sxh, syh, sxb, syb, fx[q][0], fx[q][1]);
-                    flux_down(fpn + sl[q][1] * NP, qoffy, loffy, exy, eyy, href, u, v, v, u, f0 + syh * offy,
-                              g0 + syb * offy, syh, sxh, syb, sxb, fx[q][2], fx[q][3]);
-                }
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    Fh[sl[q][0] * VB] = fx[q][0];
-                    Fb[sl[q][0] * VB] = fx[q][1];
-                    Fh[sl[q][1] * VB] = fx[q][2];
-                    Fb[sl[q][1] * VB] = fx[q][3];
-                }
-                rfirst = 2;
-            }
+            V fl[NPASS][2];
+            int fo[NPASS][2];
 #pragma unroll
             for (int r = 0; r < NPASS; ++r) {
-                if (r < rfirst) continue;
+                fo[r][0] = fo[r][1] = -1;
+                fl[r][0] = fl[r][1] = bc(T(0));
                 const int it = warp + r * NW;
                 if (it >= NIT) break;
-                int ti, tj;
-                bool dox = true, doy = true;
-                if ((r + 1) * NW <= NCT || it < NCT) {
-                    ti = it % TX; tj = it / TX;
-                    if (i0 + ti >= nx || j0 + tj >= ny) continue;
-                } else if (it < NCT + TY) {
-                    tj = it - NCT; ti = xneg ? iend - i0 : -1; doy = false;
-                    if (j0 + tj >= ny) continue;
-                } else {
-                    ti = it - NCT - TY; tj = yneg ? jend - j0 : -1; dox = false;
-                    if (i0 + ti >= nx) continue;
-                }
-                const int i = i0 + ti, j = j0 + tj;
-                if (i < 0 || i >= nx || j < 0 || j >= ny) {
+                const K4Item<T>& d = items[it];
+                const int kind = d.kind;
+                if (kind == 0) continue;
+                if (kind >= 4) {
                     // upwind face of the tile on a wall: the re-emitted distribution
-                    T Hf, Bf;
-                    int slot;
-                    if (dox) {
-                        const int fi = i < 0 ? 0 : nx;
-                        slot = tj * (TX + 1) + fi - i0;
-                        flux_wall(fpn + slot * NP, wtab + ((i < 0 ? 3 : 1) * cd.nslot + wall_slot(cd, n)) * nuv, iu,
-                                  ivn, href, u, Hf, Bf);
-                    } else {
-                        const int fj = j < 0 ? 0 : ny;
-                        slot = NFX + (fj - j0) * TX + ti;
-                        flux_wall(fpn + slot * NP, wtab + ((j < 0 ? 0 : 2) * cd.nslot + wall_slot(cd, n)) * nuv, iu,
-                                  ivn, href, v, Hf, Bf);
-                    }
-                    Fh[slot * VB] = Hf;
-                    Fb[slot * VB] = Bf;
+                    const bool xw = kind == 4;
+                    const T* tb = wtab + ((xw ? d.tx : d.ty) * cd.nslot + wall_slot(cd, n)) * nuv;
+                    fo[r][0] = xw ? d.fx : d.fy;
+                    fl[r][0] = flux_wall2(fpn + (xw ? d.px : d.py), tb, iu, ivn, href, xw ? ub : vbb);
+                    fl[r][1] = fl[r][0];
                     continue;
                 }
-                const int kx = ti - xlo, ky = tj - ylo;
-                const int fix = xneg ? i : i + 1, fjy = yneg ? j : j + 1;
-                const int slx = tj * (TX + 1) + fix - i0, sly = NFX + (fjy - j0) * TX + ti;
+                const bool dox = kind != 3, doy = kind != 2;
                 // expm1 factors of the interface Maxwellians first: their latency overlaps the reconstruction
-                const T* tbx = ftn + (j * (nx + 1) + fix) * NTf;
-                const T* tby = ftn + (nfx + fjy * nx + i) * NTf;
                 T exx = T(0), eyx = T(0), exy = T(0), eyy = T(0);
-                if (dox) { exx = __ldg(tbx + iu); eyx = __ldg(tbx + ivn); }
-                if (doy) { exy = __ldg(tby + iu); eyy = __ldg(tby + ivn); }
-                const T* ph = rh + (ky * PX + kx) * VB;
-                const T* pb = ph + lv;
-                const T f0 = ph[0], g0 = pb[0];
-                const bool hm = i > 0, hp = i < nx - 1, vm = j > 0, vp = j < ny - 1;
-                const T wxm = gxr[kx - 1], wxp = gxr[kx], wym = gyr[ky - 1], wyp = gyr[ky];
-                const T sxh = slope(ph[-VB], f0, ph[VB], wxm, wxp, hm, hp, nx > 1);
-                const T sxb = slope(pb[-VB], g0, pb[VB], wxm, wxp, hm, hp, nx > 1);
-                const T syh = slope(ph[-PX * VB], f0, ph[PX * VB], wym, wyp, vm, vp, ny > 1);
-                const T syb = slope(pb[-PX * VB], g0, pb[PX * VB], wym, wyp, vm, vp, ny > 1);
+                if (dox) { exx = __ldg(ftn + d.tx + iu); eyx = __ldg(ftn + d.tx + ivn); }
+                if (doy) { exy = __ldg(ftn + d.ty + iu); eyy = __ldg(ftn + d.ty + ivn); }
+                const V* ph = rh + d.rect;
+                const V f0 = ph[0];
+                V sxv, syv;
+                if (interior) {
+                    sxv = slope2i(ph[-VB], f0, ph[VB], d.w[0], d.w[1]);
+                    syv = slope2i(ph[-PX * VB], f0, ph[PX * VB], d.w[2], d.w[3]);
+                } else {
+                    const int fg = d.flags;
+                    sxv = slope2(ph[-VB], f0, ph[VB], d.w[0], d.w[1], (fg & 1) != 0, (fg & 2) != 0, (fg & 16) != 0);
+                    syv = slope2(ph[-PX * VB], f0, ph[PX * VB], d.w[2], d.w[3], (fg & 4) != 0, (fg & 8) != 0,
+                                 (fg & 32) != 0);
+                }
                 if (dox) {
-                    const T off = xneg ? -gxh[kx] : gxh[kx];
-                    T Hf, Bf;
-                    flux_down(fpn + slx * NP, qoff, loff, exx, eyx, href, u, v, u, v, f0 + sxh * off, g0 + sxb * off,
-                              sxh, syh, sxb, syb, Hf, Bf);
-                    Fh[slx * VB] = Hf;
-                    Fb[slx * VB] = Bf;
+                    fo[r][0] = d.fx;
+                    fl[r][0] = flux2(fpn + d.px, qoff, loff, exx, eyx, u, v, hb, ub, vbb, pfma(sxv, bc(d.w[4]), f0),
+                                     sxv, syv);
                 }
                 if (doy) {
-                    const T off = yneg ? -gyh[ky] : gyh[ky];
-                    T Hf, Bf;
-                    flux_down(fpn + sly * NP, qoffy, loffy, exy, eyy, href, u, v, v, u, f0 + syh * off, g0 + syb * off,
-                              syh, sxh, syb, sxb, Hf, Bf);
-                    Fh[sly * VB] = Hf;
-                    Fb[sly * VB] = Bf;
+                    fo[r][1] = d.fy;
+                    fl[r][1] = flux2(fpn + d.py, qoffy, loffy, exy, eyy, u, v, hb, vbb, ub,
+                                     pfma(syv, bc(d.w[5]), f0), syv, sxv);
                 }
             }
+            // stores last, so that the items' independent chains interleave
+#pragma unroll
+            for (int r = 0; r < NPASS; ++r)
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    if (fo[r][k] >= 0) F[fo[r][k]] = fl[r][k];
         }
         if (s > 0) {
             // ---- pass 2, level s - 1: Eq. fv_h with the spectral source (delta form)
             const int n = s - 1;
-            const T* Fh = fbuf + (size_t)(n & 1) * L::FLUX + lane;
-            const T* Fb = Fh + NFT * VB;
-            T* on = cd.dh[p ^ 1] + ((size_t)vb * nt + n) * nc * VB + lane;
-            T* onb = cd.db[p ^ 1] + ((size_t)vb * nt + n) * nc * VB + lane;
+            const V* F = fbuf + (size_t)(n & 1) * L::FLUX + lane;
             const T* cpn = cps + (size_t)(n & 1) * L::CP;
             const T* ctn = ctab + n * 2 * nuv;
-            constexpr int lvo = 2 * NCT * VB;                 // level stride of the own-cell store
+            const V* fc[RC];
+            V fn[RC], e[RC];
 #pragma unroll
-            for (int r = 0; r < (NCT + NW - 1) / NW; ++r) {
-                const int ct = warp + r * NW;
-                if (ct >= NCT) break;
-                const int ti = ct % TX, tj = ct / TX;
-                const int i = i0 + ti, j = j0 + tj;
-                if (i >= nx || j >= ny) continue;
-                const int c = j * nx + i;
-                const T* tb = ctn + c * nt * 2 * nuv;
+            for (int q = 0; q < RC; ++q) {
+                fc[q] = own + (warp + q * NW) * VB + lane;
+                fn[q] = ok[q] ? fc[q][n * LVO] : bc(T(0));
+                e[q] = bc(T(0));
+            }
+            if (!implicit) {
+                const V* en = spec + n * nt;
+                switch (nt) {
+                    case 1: break;
+                    case 3: spectral_rows<3, RC, LVO>(en, fc, fn, e); break;
+                    case 5: spectral_rows<5, RC, LVO>(en, fc, fn, e); break;
+                    case 7: spectral_rows<7, RC, LVO>(en, fc, fn, e); break;
+                    case 9: spectral_rows<9, RC, LVO>(en, fc, fn, e); break;
+                    case 11: spectral_rows<11, RC, LVO>(en, fc, fn, e); break;
+                    case 13: spectral_rows<13, RC, LVO>(en, fc, fn, e); break;
+                    default: spectral_rows<15, RC, LVO>(en, fc, fn, e); break;
+                }
+            }
+            V x[RC];
+#pragma unroll
+            for (int q = 0; q < RC; ++q) {
+                if (!ok[q]) continue;
+                const T* tb = ctn + otb[q];
                 const T ex0 = __ldg(tb + iu), ey0 = __ldg(tb + ivn);
                 const T ex1 = __ldg(tb + nuv + iu), ey1 = __ldg(tb + nuv + ivn);
-                const int fL = tj * (TX + 1) + ti, fB = NFX + tj * TX + ti;
-                const T dxh = Fh[(fL + 1) * VB] - Fh[fL * VB];
-                const T dyh = Fh[(fB + TX) * VB] - Fh[fB * VB];
-                const T dxb = Fb[(fL + 1) * VB] - Fb[fL * VB];
-                const T dyb = Fb[(fB + TX) * VB] - Fb[fB * VB];
-                T* hc = own + ct * VB + lane;                // level m, array a at hc[m * lvo + a * NCT * VB]
-                T* bc = hc + NCT * VB;
-                T eh, eb;
-                switch (implicit ? 0 : nh) {
-                    case 0: eh = T(0); eb = T(0); break;
-                    case 1: spectral<1>(hc, bc, n, nt, lvo, et, eh, eb); break;
-                    case 2: spectral<2>(hc, bc, n, nt, lvo, et, eh, eb); break;
-                    case 3: spectral<3>(hc, bc, n, nt, lvo, et, eh, eb); break;
-                    case 4: spectral<4>(hc, bc, n, nt, lvo, et, eh, eb); break;
-                    case 5: spectral<5>(hc, bc, n, nt, lvo, et, eh, eb); break;
-                    case 6: spectral<6>(hc, bc, n, nt, lvo, et, eh, eb); break;
-                    default: spectral<7>(hc, bc, n, nt, lvo, et, eh, eb); break;
-                }
-                // equilibria of W^{k+1} (slot 1) and W^k (slot 0): dH = H - H_ref from the cell table, Shakhov cubic
-                const T* cp = cpn + ct * NCP;
-                T dhp[2], dbp[2];
+                const V dX = psub(F[ofl[q] + VB], F[ofl[q]]);
+                const V dY = psub(F[ofb[q] + TX * VB], F[ofb[q]]);
+                // equilibria of W^{k+1} (slot 1) and W^k (slot 0), delta form
+                const T* cp = cpn + ocp[q];
+                const V q1 = eq2(cp + C_EQ1, ex1, ey1, hb, u, v, r2, shakhov);
+                const V q0 = eq2(cp + C_EQ0, ex0, ey0, hb, u, v, r2, shakhov);
+                const V* k = reinterpret_cast<const V*>(cp + C_K);   // kself, -kE, kp1, kp0, -kdx, -kdy
+                V y = pmul(k[0], fn[q]);
+                y = pfma(k[4], dX, y);
+                y = pfma(k[5], dY, y);
+                y = pfma(k[1], e[q], y);
+                y = pfma(k[2], q1, y);
+                x[q] = pfma(k[3], q0, y);
+            }
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const T* q = cp + (e == 0 ? C_EQ0 : C_EQ1);
-                    const T ex = e == 0 ? ex0 : ex1, ey = e == 0 ? ey0 : ey1;
-                    const T E = ex + ey + ex * ey;
-                    const T dH = href * (q[E_RM1] + q[E_R] * E);
-                    const T dB = dH * q[E_I2L] + href * q[E_DI2L];
-                    if (shakhov) {
-                        const T H = href + dH;
-                        const T sk = cubic(q + E_SH, u, v);
-                        const T skb = sk + q[E_SHB] + q[E_SHB + 1] * u + q[E_SHB + 2] * v;
-                        dhp[e] = dH + H * sk;
-                        dbp[e] = dB + H * q[E_I2L] * skb;
-                    } else {
-                        dhp[e] = dH;
-                        dbp[e] = dB;
-                    }
-                }
-                const T* k = cp + C_KSELF;                    // kself, kE, kp1, kp0, kdx, kdy
-                const T h0 = hc[n * lvo], b0 = bc[n * lvo];
-                const T xh = k[0] * h0 - k[4] * dxh - k[5] * dyh - k[1] * eh + k[2] * dhp[1] + k[3] * dhp[0];
-                const T xb = k[0] * b0 - k[4] * dxb - k[5] * dyb - k[1] * eb + k[2] * dbp[1] + k[3] * dbp[0];
-                if (implicit) {
-                    // right-hand side of level n; h^k of this level is no longer needed
-                    hc[n * lvo] = xh;
-                    bc[n * lvo] = xb;
-                } else {
-                    on[c * VB] = xh;
-                    onb[c * VB] = xb;
-                }
+            for (int q = 0; q < RC; ++q) {
+                if (!ok[q]) continue;
+                if (implicit) const_cast<V*>(fc[q])[n * LVO] = x[q];   // right-hand side of level n
+                else cd.f[p ^ 1][((size_t)vb * nt + n) * nc * VB + (size_t)oc[q] * VB + lane] = x[q];
             }
         }
         __syncthreads();
     }
     if (implicit) {
-        // spectral source at the new iterate: h^{k+1} = minv (right-hand sides over the levels), per cell and lane
-        constexpr int lvo = 2 * NCT * VB;
+        // spectral source at the new iterate: f^{k+1} = minv (right-hand sides over the levels), per cell and lane
         for (int ct = warp; ct < NCT; ct += NW) {
             const int ti = ct % TX, tj = ct / TX;
             const int i = i0 + ti, j = j0 + tj;
             if (i >= nx || j >= ny) continue;
             const int c = j * nx + i;
-            const T* hc = own + ct * VB + lane;
-            const T* bc = hc + NCT * VB;
-            T rh[MAXNT], rb[MAXNT];
+            const V* fcc = own + ct * VB + lane;
+            V rr[MAXNT];
 #pragma unroll
-            for (int m = 0; m < MAXNT; ++m) {
-                rh[m] = m < nt ? hc[m * lvo] : T(0);
-                rb[m] = m < nt ? bc[m * lvo] : T(0);
-            }
+            for (int m = 0; m < MAXNT; ++m) rr[m] = m < nt ? fcc[m * LVO] : bc(T(0));
             const T* Mi = cd.minv + (size_t)c * nt * nt;
-            T* oh = cd.dh[p ^ 1] + (size_t)vb * nt * nc * VB + (size_t)c * VB + lane;
-            T* ob = cd.db[p ^ 1] + (size_t)vb * nt * nc * VB + (size_t)c * VB + lane;
+            V* o = cd.f[p ^ 1] + (size_t)vb * nt * nc * VB + (size_t)c * VB + lane;
 #pragma unroll
             for (int n = 0; n < MAXNT; ++n) {
                 if (n >= nt) break;
-                T sh = T(0), sb = T(0);
+                V acc = bc(T(0));
 #pragma unroll
                 for (int m = 0; m < MAXNT; ++m)
-                    if (m < nt) {
-                        const T w = __ldg(Mi + n * nt + m);
-                        sh += w * rh[m];
-                        sb += w * rb[m];
-                    }
-                oh[(size_t)n * nc * VB] = sh;
-                ob[(size_t)n * nc * VB] = sb;
+                    if (m < nt) acc = pfma(bc(__ldg(Mi + n * nt + m)), rr[m], acc);
+                o[(size_t)n * nc * VB] = acc;
             }
         }
     }

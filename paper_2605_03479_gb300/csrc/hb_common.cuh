@@ -1,7 +1,7 @@
 // Shared device definitions of the GB300 HB-UGKS path.
 //
 // State layout (per case), velocity-blocked "delta form":
-//   dh[vb][level][cell][32]   dh = h - H_ref  (T = double or float),  same for db = b - B_ref
+//   f[vb][level][cell][32] = (h - H_ref, b - B_ref)   pairs of T = double or float, h and b side by side
 // with vb the block of 32 consecutive discrete velocities (one warp lane per velocity), cell = j*nx + i and
 // H_ref = (lam0/pi) exp(-lam0 |u|^2), B_ref = H_ref / (2 lam0), the reduced Maxwellian at rest at T0
 // (lam0 = 1).  Every update is applied to the deviations, which is algebraically identical to the update of
@@ -19,10 +19,46 @@ constexpr int MAXNT = 15;     // N_H <= 7
 constexpr int NM = 23;        // face moments per (face, level)
 constexpr int NCM = 13;       // cell moments per (cell, level)
 constexpr int NP = 44;        // face parameters per (face, level), 16-byte aligned blocks
-constexpr int NCP = 48;       // cell parameters per (cell, level)
+constexpr int NCP = 36;       // cell parameters per (cell, level)
 constexpr int RING = 4096;    // residual history slots per case
 constexpr int K3_THREADS = 128;
 constexpr int WCN = 18;       // per wall and level: Aw[13] (reflected-half raw moments, unit density), Dw, Gw[4]
+
+// ------------------------------------------------------------------ (h, b) pairs and packed arithmetic
+// The reduced distributions h and b of one velocity go through the same transport, reconstruction, spectral and
+// update arithmetic, so they are stored and processed as a pair.  For float a pair is one 64-bit register pair
+// and every operation below is a single packed FP32x2 instruction of sm_100+ (both halves rounded as the
+// scalar instruction would); for double they are two scalar operations.
+template <typename T> struct PairOf;
+template <> struct PairOf<float> { using type = float2; };
+template <> struct PairOf<double> { using type = double2; };
+template <typename T> using P2 = typename PairOf<T>::type;
+
+__device__ __forceinline__ float2 pk(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ double2 pk(double x, double y) { return make_double2(x, y); }
+__device__ __forceinline__ float2 bc(float x) { return make_float2(x, x); }
+__device__ __forceinline__ double2 bc(double x) { return make_double2(x, x); }
+
+__device__ __forceinline__ uint64_t f2u(float2 a) { return *reinterpret_cast<uint64_t*>(&a); }
+__device__ __forceinline__ float2 u2f(uint64_t a) { return *reinterpret_cast<float2*>(&a); }
+
+// a * b + c
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c)
+{
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
+    return u2f(d);
+}
+__device__ __forceinline__ double2 psub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 
 // Face parameter slots of the micro flux (delta form).  For an interface velocity u = (u, v) with normal
 // component u_n, the Maxwellian part of the time-integrated flux divided by dG_f is
@@ -33,13 +69,15 @@ constexpr int WCN = 18;       // per wall and level: Aw[13] (reflected-half raw 
 // Cubic monomial order: 1, u, v, u^2, uv, v^2, u^3, u^2 v, u v^2, v^3.  Blocks start on multiples of 4.
 enum FP {
     F_QL = 0, F_QR = 12, F_LBL = 24, F_LBR = 28, F_RM1 = 32, F_R = 33, F_I2L = 34, F_DI2L = 35,
-    F_C1 = 36, F_C4 = 37, F_C5 = 38, F_NIN = 39, F_WRM1 = 40, F_WR = 41, F_WI2L = 42, F_WDI2L = 43
+    F_C1 = 36, F_C4 = 37, F_C5 = 38, F_C1D = 39, F_WRM1 = 40, F_WR = 41, F_WI2L = 42, F_WDI2L = 43
 };
-// Cell parameter slots: equilibrium of W^k at 0..19, of W^{k+1} at 20..39 (each: r - 1, r, 1/(2 lam),
-// 1/(2 lam) - 1/(2 lam0), Shakhov cubic s (c.q)(2 lam |c|^2 - 4) [10] at 4, b-part linear term 2 s (c.q) [3]
-// at 16), update coefficients of Eq. fv_h at 40..45.
-enum CP { C_EQ0 = 0, C_EQ1 = 20, C_KSELF = 40, C_KE, C_KP1, C_KP0, C_KDX, C_KDY };
-enum EQ { E_RM1 = 0, E_R, E_I2L, E_DI2L, E_SH = 4, E_SHB = 16 };
+// Cell parameter slots: equilibrium of W^k at 0..11, of W^{k+1} at 12..23, each: r - 1, r, 1/(2 lam),
+// 1/(2 lam) - 1/(2 lam0), then the Shakhov factor s (c.q)(2 lam |c|^2 - 4) = L(u, v) Q(u, v) as
+// L = a0 + a1 u + a2 v (slots 4..6; 7 unused) and Q = b0 + b1 u + b2 v + b3 (u^2 + v^2) (slots 8..11): the reduced
+// corrections are H+ = L Q H and B+ = (L Q + 2 L) B.  From 24 on, the update coefficients of Eq. fv_h as
+// broadcast pairs (each value twice): kself, -kE, kp1, kp0, -kdx, -kdy.
+enum CP { C_EQ0 = 0, C_EQ1 = 12, C_K = 24 };
+enum EQ { E_RM1 = 0, E_R, E_I2L, E_DI2L, E_L = 4, E_Q = 8 };
 
 struct CaseStatus {
     int active;          // iterating in the current call
@@ -67,6 +105,7 @@ struct CaseDev {
     const double *xn, *yn, *xc, *yc, *hx, *hy, *rdx, *rdy;   // rdx[i] = 1/(xc[i+1]-xc[i])
     const double *vu, *vv, *vw;        // per padded velocity
     const T *tu, *tv, *tw, *thref;     // per padded velocity
+    const T *twu, *twv;                // per padded velocity: the factors w_u, w_v of its weight (0 for padding)
     const double *u1, *wu1, *v1, *wv1; // 1-D grids
     const T *tu1, *tv1;                // 1-D nodes in the storage precision
     const double* refmom;              // [5][13]: full, u>0, u<0, v>0, v<0 moments of (H_ref, B_ref)
@@ -75,8 +114,7 @@ struct CaseDev {
     const T *xr0t, *yr0t;              // the same in the storage precision
     const double* wconst;              // [4][nslot][WCN] reflected-half constants of each wall Maxwellian
     const double* oconst;              // [4][8]: incident and reflected flux moments of (H_ref, B_ref) per wall
-    T* dh[2];
-    T* db[2];
+    P2<T>* f[2];                       // the two state buffers (current: st->parity)
     double* W[2];
     double* dG;
     double* hmom;                      // [nc][nt][4][NM] half-face sums of the reconstruction per sign class
@@ -218,42 +256,6 @@ __device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t phase)
     }
 }
 
-// ------------------------------------------------------------------ (h, b) pairs and packed arithmetic
-// The reduced distributions h and b of one velocity go through the same transport, reconstruction, spectral and
-// update arithmetic, so they are stored and processed as a pair.  For float a pair is one 64-bit register pair
-// and every operation below is a single packed FP32x2 instruction of sm_100+ (both halves rounded as the
-// scalar instruction would); for double they are two scalar operations.
-template <typename T> struct PairOf;
-template <> struct PairOf<float> { using type = float2; };
-template <> struct PairOf<double> { using type = double2; };
-template <typename T> using P2 = typename PairOf<T>::type;
-
-__device__ __forceinline__ float2 pk(float x, float y) { return make_float2(x, y); }
-__device__ __forceinline__ double2 pk(double x, double y) { return make_double2(x, y); }
-__device__ __forceinline__ float2 bc(float x) { return make_float2(x, x); }
-__device__ __forceinline__ double2 bc(double x) { return make_double2(x, x); }
-
-__device__ __forceinline__ uint64_t f2u(float2 a) { return *reinterpret_cast<uint64_t*>(&a); }
-__device__ __forceinline__ float2 u2f(uint64_t a) { return *reinterpret_cast<float2*>(&a); }
-
-// a * b + c
-__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c)
-{
-    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
-}
-__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
-__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 psub(float2 a, float2 b)
-{
-    uint64_t d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)));
-    return u2f(d);
-}
-__device__ __forceinline__ double2 psub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-
 template <typename T> __device__ __forceinline__ T t_expm1(T x);
 template <> __device__ __forceinline__ double t_expm1<double>(double x) { return expm1(x); }
 template <> __device__ __forceinline__ float t_expm1<float>(float x) { return expm1f(x); }
@@ -344,7 +346,9 @@ __device__ inline void shakhov_poly(double s, double qx, double qy, double U, do
     o[12] = 2.0 * a2;
 }
 
-// Cell equilibrium parameters (slots E_*) of the Maxwellian (rho, U, V, lam) with heat flux q
+// Cell equilibrium parameters (slots E_*) of the Maxwellian (rho, U, V, lam) with heat flux q: the Shakhov
+// factor s (c.q)(2 lam |c|^2 - 4), s = (1 - Pr) 4 lam^2 / (5 rho), c = u - U, kept as its linear factor
+// L = s (c.q) and quadratic factor 2 lam |c|^2 - 4 (Eq. shakhov integrated over xi)
 template <typename T>
 __device__ inline void eq_cell(double rho, double U, double V, double lam, double lam0, double pr, double qx, double qy,
                                T* o)
@@ -354,12 +358,15 @@ __device__ inline void eq_cell(double rho, double U, double V, double lam, doubl
     o[E_R] = T(r);
     o[E_I2L] = T(0.5 / lam);
     o[E_DI2L] = T(0.5 / lam - 0.5 / lam0);
-    double sp[13];
-    shakhov_poly((1.0 - pr) * 4.0 * lam * lam / (5.0 * rho), qx, qy, U, V, lam, sp);
-#pragma unroll
-    for (int k = 0; k < 10; ++k) o[E_SH + k] = T(sp[k]);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) o[E_SHB + k] = T(sp[10 + k]);
+    const double s = (1.0 - pr) * 4.0 * lam * lam / (5.0 * rho);
+    o[E_L] = T(-s * (qx * U + qy * V));
+    o[E_L + 1] = T(s * qx);
+    o[E_L + 2] = T(s * qy);
+    o[E_L + 3] = T(0);
+    o[E_Q] = T(2.0 * lam * (U * U + V * V) - 4.0);
+    o[E_Q + 1] = T(-4.0 * lam * U);
+    o[E_Q + 2] = T(-4.0 * lam * V);
+    o[E_Q + 3] = T(2.0 * lam);
 }
 
 // Horner evaluation of the bivariate cubic with monomials 1, u, v, u^2, uv, v^2, u^3, u^2 v, u v^2, v^3

@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
     pp[F_C1] = C1p;
     pp[F_C4] = T(C[3] / dGf);
     pp[F_C5] = T(C[4] / dGf);
-    pp[F_NIN] = T(nin);
+    pp[F_C1D] = T(C[0] / dGf * di2l);                      // C1' (1/(2 lam) - 1/(2 lam0))
     if (wall) {
         const double* ws = cd.wall + ((size_t)g.wall * cd.nslot + wsl) * 3;
         const double lamw = cd.lam0 / ws[2];
@@ -404,16 +404,6 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
 // rho: H - H_ref = H_ref [(r - 1) + r (ex + ey + ex ey)], r = rho lam / lam0.  One warp per face-level (interface
 // and, at walls, reflected Maxwellian) or cell-level (W^k and W^{k+1}); lanes over the nodes.
 template <typename T>
-__device__ __forceinline__ void fill_table(T* dst, const T* x1, int n, double lam0, double lam, double U, int lane)
-{
-    const T dl = T(lam0 - lam), tl = T(2.0 * lam * U), lu2 = T(lam * U * U);
-    for (int k = lane; k < n; k += 32) {
-        const T x = x1[k];
-        dst[k] = t_expm1<T>(dl * x * x + tl * x - lu2);
-    }
-}
-
-template <typename T>
 __global__ void __launch_bounds__(128) k_tables(Batch<T> B)
 {
     const int cs = find_case(B.off, B.ncases, blockIdx.x);
@@ -424,12 +414,31 @@ __global__ void __launch_bounds__(128) k_tables(Batch<T> B)
     const int nt = cd.nt, nuv = cd.nu + cd.nv;
     if (item >= cd.nc * nt) return;
     const int p = cd.st->parity;
-    for (int e = 0; e < 2; ++e) {
+    // lane e < 2 forms the exponent coefficients of W^k (e = 0) and W^{k+1} (e = 1) once (FP64 divisions are
+    // slow), the warp shares them
+    T q[5] = {T(0), T(0), T(0), T(0), T(0)};
+    if (lane < 2) {
         double rho, U, V, lam;
-        prim((e == 0 ? cd.W[p] : cd.W[p ^ 1]) + ((size_t)(item % nt) * cd.nc + item / nt) * 4, rho, U, V, lam);
+        prim((lane == 0 ? cd.W[p] : cd.W[p ^ 1]) + ((size_t)(item % nt) * cd.nc + item / nt) * 4, rho, U, V, lam);
+        q[0] = T(cd.lam0 - lam);
+        q[1] = T(2.0 * lam * U);
+        q[2] = T(lam * U * U);
+        q[3] = T(2.0 * lam * V);
+        q[4] = T(lam * V * V);
+    }
+    for (int e = 0; e < 2; ++e) {
+        T c[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) c[k] = __shfl_sync(0xffffffffu, q[k], e);
         T* dst = cd.ctab + ((size_t)item * 2 + e) * nuv;
-        fill_table(dst, cd.tu1, cd.nu, cd.lam0, lam, U, lane);
-        fill_table(dst + cd.nu, cd.tv1, cd.nv, cd.lam0, lam, V, lane);
+        for (int k = lane; k < cd.nu; k += 32) {
+            const T x = cd.tu1[k];
+            dst[k] = t_expm1<T>(c[0] * x * x + c[1] * x - c[2]);
+        }
+        for (int k = lane; k < cd.nv; k += 32) {
+            const T y = cd.tv1[k];
+            dst[cd.nu + k] = t_expm1<T>(c[0] * y * y + c[3] * y - c[4]);
+        }
     }
 }
 
@@ -593,12 +602,11 @@ __global__ void __launch_bounds__(K3_THREADS) k3_macro(Batch<T> B)
             const double D = 1.0 + 0.5 * dG / t1;
             Dn[n] = D;
             const double s_ = implicit ? 1.0 : D;
-            cp[C_KSELF] = T((1.0 - 0.5 * dG / t0) / s_);
-            cp[C_KE] = T(implicit ? 0.0 : dG * cd.omega / D);
-            cp[C_KP1] = T(0.5 * dG / (t1 * s_));
-            cp[C_KP0] = T(0.5 * dG / (t0 * s_));
-            cp[C_KDX] = T(dG / (dx * s_));
-            cp[C_KDY] = T(dG / (dy * s_));
+            // kself, -kE, kp1, kp0, -kdx, -kdy, each stored twice (broadcast pairs for the (h, b) update)
+            const double kk[6] = {(1.0 - 0.5 * dG / t0) / s_, implicit ? 0.0 : -dG * cd.omega / D,
+                                  0.5 * dG / (t1 * s_), 0.5 * dG / (t0 * s_), -dG / (dx * s_), -dG / (dy * s_)};
+#pragma unroll
+            for (int q = 0; q < 6; ++q) cp[C_K + 2 * q] = cp[C_K + 2 * q + 1] = T(kk[q]);
         }
         if (implicit) {
             // inverse of diag(D_n) + dG omega E for the micro update of this cell (every velocity)
@@ -700,8 +708,8 @@ __global__ void k_set_level(CaseDev<T> cd, int n, int which, const double* stage
         double rv = which == 0 ? href : href * 0.5 / cd.lam0;
         val = stage[(size_t)c * cd.nvel + can] - rv;
     }
-    T* dst = which == 0 ? cd.dh[cd.st->parity] : cd.db[cd.st->parity];
-    dst[sidx(cd.nc, cd.nt, vb, c, n, lane)] = T(val);
+    T* dst = reinterpret_cast<T*>(cd.f[cd.st->parity]);
+    dst[2 * sidx(cd.nc, cd.nt, vb, c, n, lane) + which] = T(val);
 }
 
 template <typename T>
@@ -719,8 +727,8 @@ __global__ void k_get_level(CaseDev<T> cd, int n, int which, double* stage)
     if (can < 0 || cd.vcls[vb] != first_class(cd, can)) return;
     double href = (cd.lam0 / M_PI) * exp(-cd.lam0 * (cd.vu[a] * cd.vu[a] + cd.vv[a] * cd.vv[a]));
     double rv = which == 0 ? href : href * 0.5 / cd.lam0;
-    const T* src = which == 0 ? cd.dh[cd.st->parity] : cd.db[cd.st->parity];
-    stage[(size_t)c * cd.nvel + can] = (double)src[sidx(cd.nc, cd.nt, vb, c, n, lane)] + rv;
+    const T* src = reinterpret_cast<const T*>(cd.f[cd.st->parity]);
+    stage[(size_t)c * cd.nvel + can] = (double)src[2 * sidx(cd.nc, cd.nt, vb, c, n, lane) + which] + rv;
 }
 
 // uniform reduced Maxwellian (rho, U, V, T) on every level, delta form; W = its continuous moments
@@ -750,8 +758,7 @@ __global__ void k_init_uniform(CaseDev<T> cd, double rho, double U, double V, do
         dhv = H - href;
         dbv = H * 0.5 / lam - href * 0.5 / cd.lam0;
     }
-    cd.dh[p][sidx(cd.nc, cd.nt, vb, c, n, lane)] = T(dhv);
-    cd.db[p][sidx(cd.nc, cd.nt, vb, c, n, lane)] = T(dbv);
+    cd.f[p][sidx(cd.nc, cd.nt, vb, c, n, lane)] = pk(T(dhv), T(dbv));
 }
 
 // fields of one level from the moments of h, b: out[f * nc + c], f = rho, U, V, T, tau_xy, qx, qy, p
@@ -768,8 +775,8 @@ __global__ void k_fields(CaseDev<T> cd, int n, double* out)
     for (int vb = 0; vb < cd.nvb; ++vb) {
         int a = vb * VB + lane;
         double w = cd.vw[a], u = cd.vu[a], v = cd.vv[a];
-        size_t id = sidx(cd.nc, cd.nt, vb, c, n, lane);
-        double wd = w * (double)cd.dh[p][id], we = w * (double)cd.db[p][id];
+        const P2<T> fv = cd.f[p][sidx(cd.nc, cd.nt, vb, c, n, lane)];
+        double wd = w * (double)fv.x, we = w * (double)fv.y;
         A[0] += wd; A[1] += wd * u; A[2] += wd * v; A[3] += wd * u * u; A[4] += wd * u * v; A[5] += wd * v * v;
         A[6] += wd * u * u * u; A[7] += wd * u * u * v; A[8] += wd * u * v * v; A[9] += wd * v * v * v;
         A[10] += we; A[11] += we * u; A[12] += we * v;

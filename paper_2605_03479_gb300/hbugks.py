@@ -61,7 +61,8 @@ EXPORTED = ("hbugks_workspace_bytes", "hbugks_create", "hbugks_destroy", "hbugks
             "hbugks_residual_history", "hbugks_get_level_fields", "hbugks_get_harmonic", "hbugks_iteration_count",
             "hbugks_status_string", "hbugks_enqueue_iterations", "hbugks_profile_kernels",
             "hbugks_harmonic_noalloc", "hbugks_launches_per_iteration", "hbugks_get_tile_shape",
-            "hbugks_set_tile_shape", "hbugks_cuda_error_string", "hbugks_test_expire_wait")
+            "hbugks_set_tile_shape", "hbugks_cuda_error_string", "hbugks_test_expire_wait",
+            "hbugks_copy_state", "hbugks_set_loop_mode")
 
 
 def lib():
@@ -102,6 +103,8 @@ def lib():
             L.hbugks_get_tile_shape.argtypes = [vp, i, C.POINTER(i), C.POINTER(i)]
             L.hbugks_set_tile_shape.argtypes = [vp, i, i, i]
             L.hbugks_test_expire_wait.argtypes = [vp]
+            L.hbugks_copy_state.argtypes = [vp, i, vp, i]
+            L.hbugks_set_loop_mode.argtypes = [vp, i]
             for name in EXPORTED:
                 if name not in ("hbugks_workspace_bytes", "hbugks_destroy", "hbugks_iteration_count",
                                 "hbugks_status_string", "hbugks_cuda_error_string"):
@@ -236,6 +239,14 @@ class Solver:
         rc = lib().hbugks_iterate(self.h, int(max_iters), float(tol_rho), its, _dp(res))
         _check(rc, "hbugks_iterate", allow=(OK, NOT_CONVERGED, DIVERGED, TIMEOUT))
         return rc, np.array(its[:], dtype=np.int64), res
+
+    def set_loop_mode(self, mode: int):
+        """0: device-side loop (one graph launch per call), 1: host-polled graphs of 16 iterations."""
+        _check(lib().hbugks_set_loop_mode(self.h, int(mode)), "hbugks_set_loop_mode")
+
+    def copy_state_from(self, case_index: int, other: "Solver", other_case: int = 0):
+        """Take the state of `other`'s case (converted to this handle's precision); see hbugks_copy_state."""
+        _check(lib().hbugks_copy_state(self.h, case_index, other.h, other_case), "hbugks_copy_state")
 
     def test_expire_wait(self):
         """Make the next iteration's micro update report its first (completed) wait as expired."""
