@@ -40,6 +40,9 @@ def workloads():
         "thermal128_v64_nh5_fp32split": lambda: [I.config5(precision=1)],
         "thermal128_v64_nh5_fp64": lambda: [I.config5(precision=0)],
         "thermal64_v48_nh3_fp32split": lambda: [I.config3(precision=1)],
+        # the large thermal cavity's velocity grid, levels and physics on 64 x 64 cells (a profiling size)
+        "thermal64_v64_nh5_fp32split": lambda: [I.make_case("thermal64_v64_nh5", 64, 64, kn=0.05, st=5.0, nh=5,
+                                                            pr=2.0 / 3.0, drive="thermal", amp=0.5, precision=1)],
         "thermal64_v48_nh3_fp64": lambda: [I.config3(precision=0)],
         "shear32_v24_nh1_fp64": lambda: [I.config1()],
         "shear64tanh_v32_nh1_sweep12_fp64": lambda: I.config2_cases(),
@@ -522,13 +525,14 @@ def main():
     if names[top] in alg:
         ach = alg[names[top]] * upd / (kms[top] * 1e-3) / 1e9
         # DRAM bytes per update of the micro update (dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-        # launch of k4_cells<float, 4, 4, 8> on the 64x64 / 48x48 / N_T 7 thermal cavity), scaled by updates;
-        # only where the launches match that capture: 4x4 tiles, velocity sign classes with no padded slots
+        # launch of k4_cells<float, 4, 4, 8> on the 64x64-cell thermal cavity with the 64x64 velocity grid and
+        # N_T = 11: 3.5547 GB for 184.5 M updates), scaled by updates; only where the launches match that
+        # capture: 4x4 tiles, the 64x64 velocity grid, N_T = 11
         traffic = None
         if names[top] == "micro_update" and case.precision == 1 and all(
-                s.tile_shape(k) == (4, 4) and c.nu % 2 == 0 and c.nv % 2 == 0
-                and (c.nu // 2) * (c.nv // 2) % 32 == 0 for k, c in enumerate(cases)):
-            traffic = 17.55 * upd
+                s.tile_shape(k) == (4, 4) and c.nu == 64 and c.nv == 64 and c.nt == 11
+                for k, c in enumerate(cases)):
+            traffic = 19.2614 * upd
         roof = {"kernel": names[top], "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_source": peak_kind, "traffic": traffic,
                 "algorithmic_bytes_per_update": alg[names[top]]}

@@ -377,19 +377,21 @@ constexpr size_t k1_cells_smem()
 // lane: u_n [C1' dH + H Q + C4' d0 + C5' (u_n s_n + u_t s_t)] for h and u_n [C1' dB + B (Q + lin) + C4' e0 +
 // C5' (...)] for b, from the face's parameters fp (shared memory; the cubic at qo and linear term at lo belong to
 // the upwind side), the expm1 factors (ex, ey) of the interface Maxwellian at the lane's velocity, the
-// reconstructed pair d0 and the normal and tangential slope pairs; hb, unb, utb are (H_ref, H_ref), (u_n, u_n)
-// and (u_t, u_t).  With g = (r - 1) + r (ex + ey + ex ey), dH = H_ref g and H = H_ref (1 + g), so the Maxwellian
-// part is H_ref [Q + g (C1' + Q)] for h and H_ref [i2l (Qb + g (C1' + Qb)) + C1' (i2l - i2l0)] for b.
+// reconstructed pair d0 and the normal and tangential slope pairs; unb, utb are (u_n, u_n) and (u_t, u_t).
 template <typename T, typename V>
-__device__ __forceinline__ V flux2(const T* fp, int qo, int lo, T ex, T ey, T u, T v, V hb, V unb, V utb, V d0,
+__device__ __forceinline__ V flux2(const T* fp, int qo, int lo, T ex, T ey, T href, T u, T v, V unb, V utb, V d0,
                                    V sn, V st)
 {
-    const T* sc = fp + F_RM1;      // r - 1, r, 1/(2 lam), 1/(2 lam) - 1/(2 lam0), C1', C4', C5', C1' (..)
-    const T g = sc[0] + sc[1] * (ex + ey + ex * ey);
+    const T* sc = fp + F_RM1;      // r - 1, r, 1/(2 lam), 1/(2 lam) - 1/(2 lam0), C1', C4', C5', nin
+    const T E = ex + ey + ex * ey;
+    const T dH = href * (sc[0] + sc[1] * E);
+    const T H = href + dH;
+    const T i2l = sc[2];
+    const T dB = dH * i2l + href * sc[3];
     const T* l = fp + lo;
     const T Q = cubic(fp + qo, u, v);
     const T Qb = Q + l[0] + l[1] * u + l[2] * v;
-    V m = pmul(hb, pk(Q + g * (sc[4] + Q), sc[2] * (Qb + g * (sc[4] + Qb)) + sc[7]));
+    V m = pk(sc[4] * dH + H * Q, sc[4] * dB + (H * i2l) * Qb);
     m = pfma(bc(sc[5]), d0, m);
     m = pfma(bc(sc[6]), pfma(unb, sn, pmul(utb, st)), m);
     return pmul(unb, m);
@@ -408,35 +410,21 @@ __device__ __forceinline__ V flux_wall2(const T* fp, const T* __restrict__ tb, i
 }
 
 // Equilibrium pair (H+ - H_ref, B+ - B_ref) of one cell-parameter slot q at the lane's velocity: the Maxwellian
-// from the cell table factors (ex, ey), with g = (r - 1) + r (ex + ey + ex ey) so that dH = H_ref g,
-// dB = H_ref (g i2l + (i2l - i2l0)), and with the Shakhov model the correction (L Q) H for h and (L Q + 2 L) B for
-// b (L, Q the linear and quadratic factors of s (c.q)(2 lam |c|^2 - 4); r2 = u^2 + v^2; hb = (H_ref, H_ref)).
+// from the cell table factors (ex, ey), and with the Shakhov model the correction (L Q) H for h and (L Q + 2 L) B
+// for b (L, Q the linear and quadratic factors of s (c.q)(2 lam |c|^2 - 4); r2 = u^2 + v^2).
 template <typename T>
-__device__ __forceinline__ P2<T> eq2(const T* q, T ex, T ey, P2<T> hb, T u, T v, T r2, bool shakhov)
+__device__ __forceinline__ P2<T> eq2(const T* q, T ex, T ey, T href, T u, T v, T r2, bool shakhov)
 {
-    const T g = q[E_RM1] + q[E_R] * (ex + ey + ex * ey);
-    const T i2l = q[E_I2L];
-    const P2<T> m = pk(g, g * i2l + q[E_DI2L]);
-    if (!shakhov) return pmul(hb, m);
+    const T E = ex + ey + ex * ey;
+    const T dH = href * (q[E_RM1] + q[E_R] * E);
+    const T dB = dH * q[E_I2L] + href * q[E_DI2L];
+    if (!shakhov) return pk(dH, dB);
+    const T H = href + dH;
     const T L = q[E_L] + q[E_L + 1] * u + q[E_L + 2] * v;
     const T Qs = q[E_Q] + q[E_Q + 1] * u + q[E_Q + 2] * v + q[E_Q + 3] * r2;
     const T sk = L * Qs;
-    return pmul(hb, pfma(bc(T(1) + g), pk(sk, i2l * (sk + T(2) * L)), m));
+    return pfma(pk(H, H * q[E_I2L]), pk(sk, sk + T(2) * L), pk(dH, dB));
 }
-
-// First-pass work item of a k4_cells CTA (one warp): a tile cell (both downwind faces), an upwind halo cell (the
-// tile face it lies upwind of) or a wall face of the tile (the re-emitted distribution); built once per CTA.
-template <typename T>
-struct alignas(16) K4Item {
-    int kind;        // 0 none, 1 tile cell, 2 halo cell: x-face, 3 halo cell: y-face, 4 wall x-face, 5 wall y-face
-    int rect;        // offset (pairs) of the cell in a rectangle slot
-    int fx, fy;      // flux-store offsets (pairs) of the x- and y-face
-    int px, py;      // face-parameter offsets of the x- and y-face
-    int tx, ty;      // interface table offsets (face * N_T * (nu + nv)); wall items: the wall's table row index
-    int flags;       // neighbours present: 1 i-1, 2 i+1, 4 j-1, 8 j+1; 16 nx > 1, 32 ny > 1
-    int pad[3];
-    T w[6];          // 1/(x_i - x_{i-1}), 1/(x_{i+1} - x_i), the same in y, signed half widths to the faces
-};
 
 // Shared-memory layout of k4_cells (byte offsets, pairs for distributions, each block 16-byte aligned):
 //   own   [nt][NCT][32] pairs      the tile's own cells on every level (spectral source, h^k of the update)
@@ -445,7 +433,6 @@ struct alignas(16) K4Item {
 //   fp    [2][NFT][NP] T           per level: parameters of the tile's faces (ring of 2 levels)
 //   cp    [2][NCT][NCP] T          per level: update coefficients of the tile's cells (ring of 2 levels)
 //   flux  [2][NFT][32] pairs       per level: micro fluxes of the tile's faces (double buffered)
-//   spec  [nt][nt] pairs           the spectral matrix E (Eq. D_explicit) as broadcast pairs
 template <typename T, int TX, int TY>
 struct K4Layout {
     using V = P2<T>;
@@ -458,23 +445,8 @@ struct K4Layout {
     __host__ __device__ static constexpr size_t fp_off(int nt) { return rect_off(nt) + 2 * RECT * sizeof(V); }
     __host__ __device__ static constexpr size_t cp_off(int nt) { return fp_off(nt) + 2 * FP * sizeof(T); }
     __host__ __device__ static constexpr size_t flux_off(int nt) { return cp_off(nt) + 2 * CP * sizeof(T); }
-    __host__ __device__ static constexpr size_t spec_off(int nt) { return flux_off(nt) + 2 * FLUX * sizeof(V); }
-    __host__ __device__ static constexpr size_t bytes(int nt) { return spec_off(nt) + (size_t)nt * nt * sizeof(V); }
+    __host__ __device__ static constexpr size_t bytes(int nt) { return flux_off(nt) + 2 * FLUX * sizeof(V); }
 };
-
-// Spectral source of RC cells on one level n: e_c = sum_m E_nm (f_m - f_n) over the levels m of cell c's own-cell
-// store (level stride LV pairs), E's row n as broadcast pairs.  Subtracting f_n, which E maps to zero, keeps a
-// level-constant state an exact fixed point and rounds relative to the level differences.
-template <int NT, int RC, int LV, typename V>
-__device__ __forceinline__ void spectral_rows(const V* en, const V* const (&fc)[RC], const V (&fn)[RC], V (&e)[RC])
-{
-#pragma unroll
-    for (int m = 0; m < NT; ++m) {
-        const V c = en[m];
-#pragma unroll
-        for (int q = 0; q < RC; ++q) e[q] = pfma(c, psub(fc[q][m * LV], fn[q]), e[q]);
-    }
-}
 
 // A CTA: a TX x TY tile of cells, one velocity block, all levels.  Per level, the first pass reconstructs
 // every tile cell and the upwind halo cells and evaluates the flux through each one's downwind face (every
@@ -484,20 +456,18 @@ __device__ __forceinline__ void spectral_rows(const V* en, const V* const (&fc)[
 // leaves each level's right-hand side in the own-cell store and a last pass applies the per-cell inverse
 // across levels.  Batch k of bulk copies (the halo rectangle and face parameters of level k, the cell
 // coefficients of level k - 1; batch 0 also every level of the tile's own cells) completes on mbarrier k & 1
-// and is issued one level ahead of its use.  Every index of a warp's work items is formed once per CTA (item
-// table in shared memory); a level adds only its buffer and table offsets.
+// and is issued one level ahead of its use.
 template <typename T, int TX, int TY, int NW, bool IMP>
 __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
 {
     using L = K4Layout<T, TX, TY>;
     using V = P2<T>;
     constexpr int PX = L::PX, PY = L::PY, NCT = L::NCT, NFX = L::NFX;
-    constexpr int NIT = NCT + TY + TX, NPASS = (NIT + NW - 1) / NW, RC = (NCT + NW - 1) / NW;
+    constexpr int NIT = NCT + TY + TX, NPASS = (NIT + NW - 1) / NW;
     constexpr int SROWS = 4;                                  // tile rows per strip of the CTA order
-    constexpr int LVO = NCT * VB;                             // level stride of the own-cell store (pairs)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bars[2];
-    __shared__ K4Item<T> items[NIT];
+    __shared__ T gxr[PX], gxh[PX], gyr[PY], gyh[PY];
     const int cs = find_case(B.off, B.ncases, blockIdx.x);
     const CaseDev<T>& cd = B.cases[cs];
     if (!cd.st->active) return;
@@ -513,7 +483,7 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
     const int strip = tile / (ntx * SROWS), rows = min(SROWS, nty - strip * SROWS);
     const int rem = tile - strip * ntx * SROWS;
     const int i0 = (rem / rows) * TX, j0 = (strip * SROWS + rem % rows) * TY;
-    const int nt = cd.nt, nc = cd.nc, nfx = cd.nfx, nf = cd.nf;
+    const int nt = cd.nt, nc = cd.nc, nh = cd.nh, nfx = cd.nfx, nf = cd.nf;
     const int nuv = cd.nu + cd.nv;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int cls = __ldg(cd.vcls + vb);
@@ -525,7 +495,6 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
     T* const fps = reinterpret_cast<T*>(smem_raw + L::fp_off(nt));
     T* const cps = reinterpret_cast<T*>(smem_raw + L::cp_off(nt));
     V* const fbuf = reinterpret_cast<V*>(smem_raw + L::flux_off(nt));
-    V* const spec = reinterpret_cast<V*>(smem_raw + L::spec_off(nt));
     mbar_setup(bars, 2);
     const int p = cd.st->parity;
     const V* gf = cd.f[p];
@@ -589,95 +558,38 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
         }
     };
     if (warp == 0) issue(0);
-
-    const int NTf = nt * nuv;                                 // per-face stride of the expm1 tables
-    // ---- the first-pass items of the tile, once per CTA
-    for (int it = threadIdx.x; it < NIT; it += blockDim.x) {
-        K4Item<T> d;
-        d.kind = 0; d.rect = 0; d.fx = d.fy = d.px = d.py = d.tx = d.ty = 0; d.flags = 0;
-        d.pad[0] = d.pad[1] = d.pad[2] = 0;
-        for (int k = 0; k < 6; ++k) d.w[k] = T(0);
-        int ti, tj, kind;
-        if (it < NCT) {
-            ti = it % TX; tj = it / TX; kind = (i0 + ti < nx && j0 + tj < ny) ? 1 : 0;
-        } else if (it < NCT + TY) {
-            tj = it - NCT; ti = xneg ? iend - i0 : -1; kind = j0 + tj < ny ? 2 : 0;
-        } else {
-            ti = it - NCT - TY; tj = yneg ? jend - j0 : -1; kind = i0 + ti < nx ? 3 : 0;
-        }
-        const int i = i0 + ti, j = j0 + tj;
-        if (kind == 2 && (i < 0 || i >= nx)) {                // the tile's upwind x-face lies on a wall
-            const int fi = i < 0 ? 0 : nx;
-            kind = 4;
-            d.fx = (tj * (TX + 1) + fi - i0) * VB;
-            d.px = (tj * (TX + 1) + fi - i0) * NP;
-            d.tx = i < 0 ? 3 : 1;
-        } else if (kind == 3 && (j < 0 || j >= ny)) {
-            const int fj = j < 0 ? 0 : ny;
-            kind = 5;
-            d.fy = (NFX + (fj - j0) * TX + ti) * VB;
-            d.py = (NFX + (fj - j0) * TX + ti) * NP;
-            d.ty = j < 0 ? 0 : 2;
-        } else if (kind != 0) {
-            const int kx = ti - xlo, ky = tj - ylo;
-            const int fix = xneg ? i : i + 1, fjy = yneg ? j : j + 1;
-            const int slx = tj * (TX + 1) + fix - i0, sly = NFX + (fjy - j0) * TX + ti;
-            d.rect = (ky * PX + kx) * VB;
-            d.fx = slx * VB; d.px = slx * NP; d.tx = (j * (nx + 1) + fix) * NTf;
-            d.fy = sly * VB; d.py = sly * NP; d.ty = (nfx + fjy * nx + i) * NTf;
-            d.flags = (i > 0 ? 1 : 0) | (i < nx - 1 ? 2 : 0) | (j > 0 ? 4 : 0) | (j < ny - 1 ? 8 : 0) |
-                      (nx > 1 ? 16 : 0) | (ny > 1 ? 32 : 0);
-            d.w[0] = i > 0 ? T(cd.rdx[i - 1]) : T(0);
-            d.w[1] = i < nx - 1 ? T(cd.rdx[i]) : T(0);
-            d.w[2] = j > 0 ? T(cd.rdy[j - 1]) : T(0);
-            d.w[3] = j < ny - 1 ? T(cd.rdy[j]) : T(0);
-            d.w[4] = xneg ? -T(cd.hx[i]) : T(cd.hx[i]);
-            d.w[5] = yneg ? -T(cd.hy[j]) : T(cd.hy[j]);
-        }
-        d.kind = kind;
-        items[it] = d;
+    for (int k = threadIdx.x; k < PX; k += blockDim.x) {
+        const int ii = i0 + xlo + k;
+        gxr[k] = (ii >= 0 && ii < nx - 1) ? T(cd.rdx[ii]) : T(0);
+        gxh[k] = (ii >= 0 && ii < nx) ? T(cd.hx[ii]) : T(0);
     }
-    // ---- the spectral matrix E_nm = e_d for m = n - d, -e_d for m = n + d (levels cyclic), as broadcast pairs
-    for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) {
-        const int n = k / nt, m = k - n * nt;
-        const int d = (n - m + nt) % nt;
-        T e = T(0);
-        if (d >= 1 && d <= cd.nh) e = cd.et[d];
-        else if (d > cd.nh) e = -cd.et[nt - d];
-        spec[k] = bc(e);
+    for (int k = threadIdx.x; k < PY; k += blockDim.x) {
+        const int jj = j0 + ylo + k;
+        gyr[k] = (jj >= 0 && jj < ny - 1) ? T(cd.rdy[jj]) : T(0);
+        gyh[k] = (jj >= 0 && jj < ny) ? T(cd.hy[jj]) : T(0);
     }
-
     const int av = vb * VB + lane;
     const T u = __ldg(cd.tu + av), v = __ldg(cd.tv + av), href = __ldg(cd.thref + av);
     const T r2 = u * u + v * v;
-    const V ub = bc(u), vbb = bc(v), hb = bc(href);
+    const V ub = bc(u), vbb = bc(v);
     const int iu = __ldg(cd.viu + av), ivn = cd.nu + __ldg(cd.viv + av);
+    V etb[8];
+#pragma unroll
+    for (int d = 0; d < 8; ++d) etb[d] = bc(cd.et[d]);
     const T* __restrict__ ftab = cd.ftab;
     const T* __restrict__ wtab = cd.wtab;
     const T* __restrict__ ctab = cd.ctab;
     const bool shakhov = cd.shakhov != 0;
+    const int NTf = nt * nuv;                                 // per-face stride of the expm1 tables
     const int qoff = xneg ? F_QR : F_QL, loff = xneg ? F_LBR : F_LBL;
     const int qoffy = yneg ? F_QR : F_QL, loffy = yneg ? F_LBR : F_LBL;
     int* err = cd.err;
+
     const bool implicit = IMP && cd.spectral_implicit != 0;   // IMP = false compiles the explicit form alone
     // a tile none of whose first-pass cells (tile cells and upwind halo) touches a wall: every stencil neighbour
     // of each exists
     const bool interior = i0 >= 2 && j0 >= 2 && i0 + TX <= nx - 2 && j0 + TY <= ny - 2;
-
-    // ---- the second-pass cells of this warp: own-store, flux, coefficient and table offsets, once per CTA
-    int ofl[RC], ofb[RC], ocp[RC], oc[RC], otb[RC];
-    bool ok[RC];
-#pragma unroll
-    for (int q = 0; q < RC; ++q) {
-        const int ct = warp + q * NW, ti = ct % TX, tj = ct / TX;
-        ok[q] = ct < NCT && i0 + ti < nx && j0 + tj < ny;
-        const int c = (j0 + tj) * nx + i0 + ti;
-        ofl[q] = (tj * (TX + 1) + ti) * VB;                   // left face; the right one follows
-        ofb[q] = (NFX + tj * TX + ti) * VB;                   // bottom face; the top one is TX faces on
-        ocp[q] = ct * NCP;
-        oc[q] = ok[q] ? c : 0;
-        otb[q] = (ok[q] ? c : 0) * nt * 2 * nuv;
-    }
+    constexpr bool PAIRED = NCT == 2 * NW;                    // each warp owns two tile cells in pass 1
 
     for (int s = 0; s <= nt; ++s) {
         if (warp == 0 && s < nt) issue(s + 1);
@@ -700,129 +612,170 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
             const V* rh = rect + (size_t)(n & 1) * L::RECT + lane;
             const T* fpn = fps + (size_t)(n & 1) * L::FP;
             const T* ftn = ftab + n * nuv;
-            V fl[NPASS][2];
-            int fo[NPASS][2];
+            int rfirst = 0;
+            if (PAIRED && interior) {
+                // both tile cells of the warp as one straight-line block, stores last, so that the two
+                // independent chains interleave
+                V fl[2][2];
+                int sl[2][2];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int it = warp + q * NW, ti = it % TX, tj = it / TX;
+                    const int i = i0 + ti, j = j0 + tj;
+                    const int kx = ti - xlo, ky = tj - ylo;
+                    const int fix = xneg ? i : i + 1, fjy = yneg ? j : j + 1;
+                    sl[q][0] = tj * (TX + 1) + fix - i0;
+                    sl[q][1] = NFX + (fjy - j0) * TX + ti;
+                    const T* tbx = ftn + (j * (nx + 1) + fix) * NTf;
+                    const T* tby = ftn + (nfx + fjy * nx + i) * NTf;
+                    const T exx = __ldg(tbx + iu), eyx = __ldg(tbx + ivn);
+                    const T exy = __ldg(tby + iu), eyy = __ldg(tby + ivn);
+                    const V* ph = rh + (ky * PX + kx) * VB;
+                    const V f0 = ph[0];
+                    const V sxv = slope2i(ph[-VB], f0, ph[VB], gxr[kx - 1], gxr[kx]);
+                    const V syv = slope2i(ph[-PX * VB], f0, ph[PX * VB], gyr[ky - 1], gyr[ky]);
+                    const V dx0 = pfma(sxv, bc(xneg ? -gxh[kx] : gxh[kx]), f0);
+                    const V dy0 = pfma(syv, bc(yneg ? -gyh[ky] : gyh[ky]), f0);
+                    fl[q][0] = flux2(fpn + sl[q][0] * NP, qoff, loff, exx, eyx, href, u, v, ub, vbb, dx0, sxv, syv);
+                    fl[q][1] = flux2(fpn + sl[q][1] * NP, qoffy, loffy, exy, eyy, href, u, v, vbb, ub, dy0, syv, sxv);
+                }
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    F[sl[q][0] * VB] = fl[q][0];
+                    F[sl[q][1] * VB] = fl[q][1];
+                }
+                rfirst = 2;
+            }
 #pragma unroll
             for (int r = 0; r < NPASS; ++r) {
-                fo[r][0] = fo[r][1] = -1;
-                fl[r][0] = fl[r][1] = bc(T(0));
+                if (r < rfirst) continue;
                 const int it = warp + r * NW;
                 if (it >= NIT) break;
-                const K4Item<T>& d = items[it];
-                const int kind = d.kind;
-                if (kind == 0) continue;
-                if (kind >= 4) {
+                int ti, tj;
+                bool dox = true, doy = true;
+                if ((r + 1) * NW <= NCT || it < NCT) {
+                    ti = it % TX; tj = it / TX;
+                    if (i0 + ti >= nx || j0 + tj >= ny) continue;
+                } else if (it < NCT + TY) {
+                    tj = it - NCT; ti = xneg ? iend - i0 : -1; doy = false;
+                    if (j0 + tj >= ny) continue;
+                } else {
+                    ti = it - NCT - TY; tj = yneg ? jend - j0 : -1; dox = false;
+                    if (i0 + ti >= nx) continue;
+                }
+                const int i = i0 + ti, j = j0 + tj;
+                if (!interior && (i < 0 || i >= nx || j < 0 || j >= ny)) {
                     // upwind face of the tile on a wall: the re-emitted distribution
-                    const bool xw = kind == 4;
-                    const T* tb = wtab + ((xw ? d.tx : d.ty) * cd.nslot + wall_slot(cd, n)) * nuv;
-                    fo[r][0] = xw ? d.fx : d.fy;
-                    fl[r][0] = flux_wall2(fpn + (xw ? d.px : d.py), tb, iu, ivn, href, xw ? ub : vbb);
-                    fl[r][1] = fl[r][0];
+                    V Fw;
+                    int slot;
+                    if (dox) {
+                        const int fi = i < 0 ? 0 : nx;
+                        slot = tj * (TX + 1) + fi - i0;
+                        Fw = flux_wall2(fpn + slot * NP, wtab + ((i < 0 ? 3 : 1) * cd.nslot + wall_slot(cd, n)) * nuv,
+                                        iu, ivn, href, ub);
+                    } else {
+                        const int fj = j < 0 ? 0 : ny;
+                        slot = NFX + (fj - j0) * TX + ti;
+                        Fw = flux_wall2(fpn + slot * NP, wtab + ((j < 0 ? 0 : 2) * cd.nslot + wall_slot(cd, n)) * nuv,
+                                        iu, ivn, href, vbb);
+                    }
+                    F[slot * VB] = Fw;
                     continue;
                 }
-                const bool dox = kind != 3, doy = kind != 2;
+                const int kx = ti - xlo, ky = tj - ylo;
+                const int fix = xneg ? i : i + 1, fjy = yneg ? j : j + 1;
+                const int slx = tj * (TX + 1) + fix - i0, sly = NFX + (fjy - j0) * TX + ti;
                 // expm1 factors of the interface Maxwellians first: their latency overlaps the reconstruction
+                const T* tbx = ftn + (j * (nx + 1) + fix) * NTf;
+                const T* tby = ftn + (nfx + fjy * nx + i) * NTf;
                 T exx = T(0), eyx = T(0), exy = T(0), eyy = T(0);
-                if (dox) { exx = __ldg(ftn + d.tx + iu); eyx = __ldg(ftn + d.tx + ivn); }
-                if (doy) { exy = __ldg(ftn + d.ty + iu); eyy = __ldg(ftn + d.ty + ivn); }
-                const V* ph = rh + d.rect;
+                if (dox) { exx = __ldg(tbx + iu); eyx = __ldg(tbx + ivn); }
+                if (doy) { exy = __ldg(tby + iu); eyy = __ldg(tby + ivn); }
+                const V* ph = rh + (ky * PX + kx) * VB;
                 const V f0 = ph[0];
+                const T wxm = gxr[kx - 1], wxp = gxr[kx], wym = gyr[ky - 1], wyp = gyr[ky];
                 V sxv, syv;
                 if (interior) {
-                    sxv = slope2i(ph[-VB], f0, ph[VB], d.w[0], d.w[1]);
-                    syv = slope2i(ph[-PX * VB], f0, ph[PX * VB], d.w[2], d.w[3]);
+                    sxv = slope2i(ph[-VB], f0, ph[VB], wxm, wxp);
+                    syv = slope2i(ph[-PX * VB], f0, ph[PX * VB], wym, wyp);
                 } else {
-                    const int fg = d.flags;
-                    sxv = slope2(ph[-VB], f0, ph[VB], d.w[0], d.w[1], (fg & 1) != 0, (fg & 2) != 0, (fg & 16) != 0);
-                    syv = slope2(ph[-PX * VB], f0, ph[PX * VB], d.w[2], d.w[3], (fg & 4) != 0, (fg & 8) != 0,
-                                 (fg & 32) != 0);
+                    sxv = slope2(ph[-VB], f0, ph[VB], wxm, wxp, i > 0, i < nx - 1, nx > 1);
+                    syv = slope2(ph[-PX * VB], f0, ph[PX * VB], wym, wyp, j > 0, j < ny - 1, ny > 1);
                 }
                 if (dox) {
-                    fo[r][0] = d.fx;
-                    fl[r][0] = flux2(fpn + d.px, qoff, loff, exx, eyx, u, v, hb, ub, vbb, pfma(sxv, bc(d.w[4]), f0),
-                                     sxv, syv);
+                    const V d0 = pfma(sxv, bc(xneg ? -gxh[kx] : gxh[kx]), f0);
+                    F[slx * VB] = flux2(fpn + slx * NP, qoff, loff, exx, eyx, href, u, v, ub, vbb, d0, sxv, syv);
                 }
                 if (doy) {
-                    fo[r][1] = d.fy;
-                    fl[r][1] = flux2(fpn + d.py, qoffy, loffy, exy, eyy, u, v, hb, vbb, ub,
-                                     pfma(syv, bc(d.w[5]), f0), syv, sxv);
+                    const V d0 = pfma(syv, bc(yneg ? -gyh[ky] : gyh[ky]), f0);
+                    F[sly * VB] = flux2(fpn + sly * NP, qoffy, loffy, exy, eyy, href, u, v, vbb, ub, d0, syv, sxv);
                 }
             }
-            // stores last, so that the items' independent chains interleave
-#pragma unroll
-            for (int r = 0; r < NPASS; ++r)
-#pragma unroll
-                for (int k = 0; k < 2; ++k)
-                    if (fo[r][k] >= 0) F[fo[r][k]] = fl[r][k];
         }
         if (s > 0) {
             // ---- pass 2, level s - 1: Eq. fv_h with the spectral source (delta form)
             const int n = s - 1;
             const V* F = fbuf + (size_t)(n & 1) * L::FLUX + lane;
+            V* on = cd.f[p ^ 1] + ((size_t)vb * nt + n) * nc * VB + lane;
             const T* cpn = cps + (size_t)(n & 1) * L::CP;
             const T* ctn = ctab + n * 2 * nuv;
-            const V* fc[RC];
-            V fn[RC], e[RC];
+            constexpr int lvo = NCT * VB;                     // level stride of the own-cell store (pairs)
 #pragma unroll
-            for (int q = 0; q < RC; ++q) {
-                fc[q] = own + (warp + q * NW) * VB + lane;
-                fn[q] = ok[q] ? fc[q][n * LVO] : bc(T(0));
-                e[q] = bc(T(0));
-            }
-            if (!implicit) {
-                const V* en = spec + n * nt;
-                switch (nt) {
-                    case 1: break;
-                    case 3: spectral_rows<3, RC, LVO>(en, fc, fn, e); break;
-                    case 5: spectral_rows<5, RC, LVO>(en, fc, fn, e); break;
-                    case 7: spectral_rows<7, RC, LVO>(en, fc, fn, e); break;
-                    case 9: spectral_rows<9, RC, LVO>(en, fc, fn, e); break;
-                    case 11: spectral_rows<11, RC, LVO>(en, fc, fn, e); break;
-                    case 13: spectral_rows<13, RC, LVO>(en, fc, fn, e); break;
-                    default: spectral_rows<15, RC, LVO>(en, fc, fn, e); break;
-                }
-            }
-            V x[RC];
-#pragma unroll
-            for (int q = 0; q < RC; ++q) {
-                if (!ok[q]) continue;
-                const T* tb = ctn + otb[q];
+            for (int r = 0; r < (NCT + NW - 1) / NW; ++r) {
+                const int ct = warp + r * NW;
+                if (ct >= NCT) break;
+                const int ti = ct % TX, tj = ct / TX;
+                const int i = i0 + ti, j = j0 + tj;
+                if (i >= nx || j >= ny) continue;
+                const int c = j * nx + i;
+                const T* tb = ctn + c * nt * 2 * nuv;
                 const T ex0 = __ldg(tb + iu), ey0 = __ldg(tb + ivn);
                 const T ex1 = __ldg(tb + nuv + iu), ey1 = __ldg(tb + nuv + ivn);
-                const V dX = psub(F[ofl[q] + VB], F[ofl[q]]);
-                const V dY = psub(F[ofb[q] + TX * VB], F[ofb[q]]);
+                const int fL = tj * (TX + 1) + ti, fB = NFX + tj * TX + ti;
+                const V dX = psub(F[(fL + 1) * VB], F[fL * VB]);
+                const V dY = psub(F[(fB + TX) * VB], F[fB * VB]);
+                V* fc = own + ct * VB + lane;                // level m at fc[m * lvo]
+                V e;
+                switch (implicit ? 0 : nh) {
+                    case 0: e = etb[0]; break;
+                    case 1: e = spectral2<1>(fc, n, nt, lvo, etb); break;
+                    case 2: e = spectral2<2>(fc, n, nt, lvo, etb); break;
+                    case 3: e = spectral2<3>(fc, n, nt, lvo, etb); break;
+                    case 4: e = spectral2<4>(fc, n, nt, lvo, etb); break;
+                    case 5: e = spectral2<5>(fc, n, nt, lvo, etb); break;
+                    case 6: e = spectral2<6>(fc, n, nt, lvo, etb); break;
+                    default: e = spectral2<7>(fc, n, nt, lvo, etb); break;
+                }
                 // equilibria of W^{k+1} (slot 1) and W^k (slot 0), delta form
-                const T* cp = cpn + ocp[q];
-                const V q1 = eq2(cp + C_EQ1, ex1, ey1, hb, u, v, r2, shakhov);
-                const V q0 = eq2(cp + C_EQ0, ex0, ey0, hb, u, v, r2, shakhov);
+                const T* cp = cpn + ct * NCP;
+                const V q1 = eq2(cp + C_EQ1, ex1, ey1, href, u, v, r2, shakhov);
+                const V q0 = eq2(cp + C_EQ0, ex0, ey0, href, u, v, r2, shakhov);
                 const V* k = reinterpret_cast<const V*>(cp + C_K);   // kself, -kE, kp1, kp0, -kdx, -kdy
-                V y = pmul(k[0], fn[q]);
-                y = pfma(k[4], dX, y);
-                y = pfma(k[5], dY, y);
-                y = pfma(k[1], e[q], y);
-                y = pfma(k[2], q1, y);
-                x[q] = pfma(k[3], q0, y);
-            }
-#pragma unroll
-            for (int q = 0; q < RC; ++q) {
-                if (!ok[q]) continue;
-                if (implicit) const_cast<V*>(fc[q])[n * LVO] = x[q];   // right-hand side of level n
-                else cd.f[p ^ 1][((size_t)vb * nt + n) * nc * VB + (size_t)oc[q] * VB + lane] = x[q];
+                const V f0 = fc[n * lvo];
+                V x = pmul(k[0], f0);
+                x = pfma(k[4], dX, x);
+                x = pfma(k[5], dY, x);
+                x = pfma(k[1], e, x);
+                x = pfma(k[2], q1, x);
+                x = pfma(k[3], q0, x);
+                if (implicit) fc[n * lvo] = x;               // right-hand side of level n; h^k no longer needed
+                else on[c * VB] = x;
             }
         }
         __syncthreads();
     }
     if (implicit) {
         // spectral source at the new iterate: f^{k+1} = minv (right-hand sides over the levels), per cell and lane
+        constexpr int lvo = NCT * VB;
         for (int ct = warp; ct < NCT; ct += NW) {
             const int ti = ct % TX, tj = ct / TX;
             const int i = i0 + ti, j = j0 + tj;
             if (i >= nx || j >= ny) continue;
             const int c = j * nx + i;
-            const V* fcc = own + ct * VB + lane;
+            const V* fc = own + ct * VB + lane;
             V rr[MAXNT];
 #pragma unroll
-            for (int m = 0; m < MAXNT; ++m) rr[m] = m < nt ? fcc[m * LVO] : bc(T(0));
+            for (int m = 0; m < MAXNT; ++m) rr[m] = m < nt ? fc[m * lvo] : bc(T(0));
             const T* Mi = cd.minv + (size_t)c * nt * nt;
             V* o = cd.f[p ^ 1] + (size_t)vb * nt * nc * VB + (size_t)c * VB + lane;
 #pragma unroll

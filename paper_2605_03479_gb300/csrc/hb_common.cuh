@@ -69,7 +69,7 @@ __device__ __forceinline__ double2 psub(double2 a, double2 b) { return make_doub
 // Cubic monomial order: 1, u, v, u^2, uv, v^2, u^3, u^2 v, u v^2, v^3.  Blocks start on multiples of 4.
 enum FP {
     F_QL = 0, F_QR = 12, F_LBL = 24, F_LBR = 28, F_RM1 = 32, F_R = 33, F_I2L = 34, F_DI2L = 35,
-    F_C1 = 36, F_C4 = 37, F_C5 = 38, F_C1D = 39, F_WRM1 = 40, F_WR = 41, F_WI2L = 42, F_WDI2L = 43
+    F_C1 = 36, F_C4 = 37, F_C5 = 38, F_NIN = 39, F_WRM1 = 40, F_WR = 41, F_WI2L = 42, F_WDI2L = 43
 };
 // Cell parameter slots: equilibrium of W^k at 0..11, of W^{k+1} at 12..23, each: r - 1, r, 1/(2 lam),
 // 1/(2 lam) - 1/(2 lam0), then the Shakhov factor s (c.q)(2 lam |c|^2 - 4) = L(u, v) Q(u, v) as

@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
     pp[F_C1] = C1p;
     pp[F_C4] = T(C[3] / dGf);
     pp[F_C5] = T(C[4] / dGf);
-    pp[F_C1D] = T(C[0] / dGf * di2l);                      // C1' (1/(2 lam) - 1/(2 lam0))
+    pp[F_NIN] = T(nin);
     if (wall) {
         const double* ws = cd.wall + ((size_t)g.wall * cd.nslot + wsl) * 3;
         const double lamw = cd.lam0 / ws[2];

@@ -87,24 +87,49 @@ CONVERGE = [
 ]
 
 
+FINISH = 300          # FP64 iterations that finish a mixed-precision run
+
+
 @pytest.mark.parametrize("name,kw,tol", CONVERGE, ids=[c[0] for c in CONVERGE])
 def test_fp32_split_harmonics_match_fp64_at_convergence(hb, name, kw, tol):
-    H = {}
-    for precision in (0, 1):
-        c = I.config3(precision=precision) if kw is None else I.make_case(name, **kw, precision=precision)
-        s = hb.Solver(c)
-        rc, its, res = s.iterate(40000, tol_rho=tol)
-        assert rc == hb.OK, (precision, its, res)
-        H[precision] = [s.harmonic(0, k) for k in range(c.n_harmonics + 1)]
-        s.destroy()
+    """Per-harmonic fields at convergence, FP32-split against FP64 after the same number of iterations N (the
+    FP64 run's count to the residual target, from rest).
+
+    * FP32-split alone: within 1e-5 of each harmonic larger than 0.1 A, and within 1e-5 max|X64| + 1e-6 A
+      otherwise (the FP32 storage floor of order 1e-7 A, which exceeds 1e-5 of the second-order harmonics).
+    * FP32-split for N - 300 iterations, then 300 FP64 iterations from its state (hbugks_copy_state): within the
+      plain 1e-5 of every harmonic k = 0..N_H of U, V, T and tau_xy; rho, q and p within 3e-5 (the level
+      harmonics of the mass, which the spectral source rotates without damping, keep part of the FP32
+      difference at the highest harmonic for thousands of iterations)."""
+    mk = (lambda p: I.config3(precision=p)) if kw is None else (lambda p: I.make_case(name, **kw, precision=p))
     amp = 0.5 if kw is None else kw["amp"]
-    for k in range(len(H[0])):
+    s64 = hb.Solver(mk(0))
+    rc, its, res = s64.iterate(40000, tol_rho=tol)
+    assert rc == hb.OK, (its, res)
+    N = int(its[0])
+    c = s64.cases[0]
+    H64 = [s64.harmonic(0, k) for k in range(c.n_harmonics + 1)]
+    s64.destroy()
+    s32 = hb.Solver(mk(1))
+    s32.iterate(N - FINISH)
+    fin = hb.Solver(mk(0))
+    fin.copy_state_from(0, s32, 0)
+    fin.iterate(FINISH)
+    Hmix = [fin.harmonic(0, k) for k in range(c.n_harmonics + 1)]
+    fin.destroy()
+    s32.iterate(FINISH)
+    H32 = [s32.harmonic(0, k) for k in range(c.n_harmonics + 1)]
+    s32.destroy()
+    for k in range(c.n_harmonics + 1):
         for f in range(8):
-            ref = np.max(np.abs(H[0][k][f]))
-            err = np.max(np.abs(H[1][k][f] - H[0][k][f]))
-            assert err <= 1e-5 * ref + 1e-6 * amp, (name, k, FIELDS[f], err, ref)
+            ref = np.max(np.abs(H64[k][f]))
+            err = np.max(np.abs(H32[k][f] - H64[k][f]))
+            assert err <= 1e-5 * ref + 1e-6 * amp, (name, "fp32", k, FIELDS[f], err, ref)
             if ref > 0.1 * amp:
-                assert err <= 1e-5 * ref, (name, k, FIELDS[f], err, ref)
+                assert err <= 1e-5 * ref, (name, "fp32", k, FIELDS[f], err, ref)
+            emix = np.max(np.abs(Hmix[k][f] - H64[k][f]))
+            bar = 1e-5 if FIELDS[f] in ("U", "V", "T", "tau_xy") else 3e-5
+            assert emix <= max(bar * ref, 1e-13), (name, "fp32+fp64", k, FIELDS[f], emix, ref)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
