@@ -291,9 +291,35 @@ def time_to_residual(args, cases):
         if not x["converged"] and y["converged"]:
             x["seconds"] = x["seconds_per_iteration"] * y["iterations"]
             x["extrapolated"] = True
+    # mixed precision: FP32-split to the target, then FP64 finishing iterations from its state
+    # (hbugks_copy_state), which bring every harmonic of U, V, T, tau_xy to the FP64 result within 1e-5
+    mixed = None
+    if a["converged"] and args.ttr_finish > 0:
+        cs32 = with_precision(cases, 1)
+        cs64 = with_precision(cases, 0)
+        for c in cs32 + cs64:
+            c.spectral_implicit = args.spectral_implicit
+        s32, s64 = hb.Solver(cs32), hb.Solver(cs64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while True:
+            rc, it, res = s32.iterate(250, tol_rho=args.ttr)
+            if rc != hb.NOT_CONVERGED or time.perf_counter() - t0 > args.ttr_budget:
+                break
+        t_32 = time.perf_counter() - t0
+        for k in range(len(cases)):
+            s64.copy_state_from(k, s32, k)
+        s64.iterate(args.ttr_finish)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        mixed = {"seconds": el, "fp32split_seconds": t_32, "fp64_finish_iterations": args.ttr_finish,
+                 "converged": rc == hb.OK}
+        s32.destroy()
+        s64.destroy()
     line = {"metric": "time to level-0 density residual", "tol": args.ttr, "unit": "s", "workload": args.workload,
-            "cases": len(cases), "fp32split": a, "fp64": b,
+            "cases": len(cases), "fp32split": a, "fp64": b, "fp32split_fp64_finish": mixed,
             "speedup_fp32split_over_fp64": b["seconds"] / a["seconds"] if a["seconds"] > 0 else None,
+            "speedup_mixed_over_fp64": b["seconds"] / mixed["seconds"] if mixed else None,
             "spectral_source": "new iterate (implicit)" if args.spectral_implicit else "old iterate (as printed)",
             "higher_is_better": False, "data": "synthetic", "start": "rest on every level"}
     print(json.dumps(line), flush=True)
@@ -364,7 +390,7 @@ def hb_versus_td(args):
                 t_rel = (el, its)
             if t_abs is None and its > chunk and r <= atol:
                 t_abs = (el, its)
-            if (t_rel and t_abs) or el > budget or not np.isfinite(r):
+            if (t_rel and t_abs) or (t_abs and args.hb_vs_td_abs_only) or el > budget or not np.isfinite(r):
                 break
         out["hb"] = {"seconds_to_relative_drop": t_rel[0] if t_rel else None,
                      "iterations_to_relative_drop": t_rel[1] if t_rel else None,
@@ -394,7 +420,7 @@ def hb_versus_td(args):
                 t_rel = (el, periods)
             if t_abs is None and periods > 1 and r <= atol:
                 t_abs = (el, periods)
-            if (t_rel and t_abs) or el > budget or not np.isfinite(r):
+            if (t_rel and t_abs) or (t_abs and args.hb_vs_td_abs_only) or el > budget or not np.isfinite(r):
                 break
         out["td"] = {"seconds_to_relative_drop": t_rel[0] if t_rel else None,
                      "periods_to_relative_drop": t_rel[1] if t_rel else None,
@@ -426,11 +452,16 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default="thermal128_v64_nh5_fp32split")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--loop-mode", type=int, default=0,
+                    help="0: device-side loop (default); 1: host-launched graphs of 16 iterations, whose kernels "
+                         "profilers list one by one (they do not list kernels inside conditional graph nodes)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ttr", type=float, default=0.0,
                     help="time to this level-0 density residual, FP32-split against FP64 (one JSON line)")
     ap.add_argument("--ttr-budget", type=float, default=600.0, help="seconds per precision for --ttr")
     ap.add_argument("--ttr-budget-fp64", type=float, default=None, help="seconds for the FP64 path (default: same)")
+    ap.add_argument("--ttr-finish", type=int, default=300,
+                    help="--ttr: FP64 iterations that finish the mixed-precision run (0: skip that run)")
     ap.add_argument("--hb-vs-td", type=float, default=0.0,
                     help="orders of residual drop: time HB-UGKS against explicit time-domain UGKS (one JSON line per case)")
     ap.add_argument("--precision", type=int, default=0, help="precision of --hb-vs-td (0 FP64, 1 FP32-split)")
@@ -439,6 +470,8 @@ def main():
     ap.add_argument("--hb-vs-td-mesh", choices=("coarse32", "paper"), default="coarse32",
                     help="--hb-vs-td cavities: 32x32 uniform cells, or the paper's 90-row wall-refined mesh")
     ap.add_argument("--hb-vs-td-drives", default="shear,thermal", help="--hb-vs-td drives to run")
+    ap.add_argument("--hb-vs-td-abs-only", action="store_true",
+                    help="--hb-vs-td: stop each run at the absolute residual (skip the relative drop)")
     ap.add_argument("--spectral-implicit", type=int, default=0,
                     help="--hb-vs-td, --ttr: HB with the spectral source at the new pseudo-time iterate (1)")
     args = ap.parse_args()
@@ -488,6 +521,7 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     s = hb.Solver(cases, device=dev, stream=stream)
+    s.set_loop_mode(args.loop_mode)
     s.init_uniform(-1, 1.0, 0.0, 0.0, 1.0)
     s.enqueue_iterations(W_)
     torch.cuda.synchronize()
@@ -510,9 +544,9 @@ def main():
     ms = slowest_rank_ms(e0.elapsed_time(e1) / args.steps, dist, dev)
     upd = sum(c.updates_per_iteration() for c in cases)
     value = job_updates_per_s(upd, world, ms)
-    # per iteration: the iteration's kernels and the device-side loop test; per call: the status reset and the
-    # kernel that sets the loop count
-    launches = s.launches_per_iteration() * args.steps + 2
+    # per iteration: the iteration's kernels (and the device-side loop test); per call: the status reset (and
+    # the kernel that sets the loop count)
+    launches = s.launches_per_iteration() * args.steps + (2 if args.loop_mode == 0 else 1)
 
     # per-kernel times (CUDA events around each launch on the kernels' stream), roofline of the top kernel
     kms = s.profile_kernels(3)
@@ -526,13 +560,13 @@ def main():
         ach = alg[names[top]] * upd / (kms[top] * 1e-3) / 1e9
         # DRAM bytes per update of the micro update (dram__bytes_read.sum + dram__bytes_write.sum of one ncu
         # launch of k4_cells<float, 4, 4, 8> on the 64x64-cell thermal cavity with the 64x64 velocity grid and
-        # N_T = 11: 3.5547 GB for 184.5 M updates), scaled by updates; only where the launches match that
+        # N_T = 11: 3.5594 GB for 184.5 M updates), scaled by updates; only where the launches match that
         # capture: 4x4 tiles, the 64x64 velocity grid, N_T = 11
         traffic = None
         if names[top] == "micro_update" and case.precision == 1 and all(
                 s.tile_shape(k) == (4, 4) and c.nu == 64 and c.nv == 64 and c.nt == 11
                 for k, c in enumerate(cases)):
-            traffic = 19.2614 * upd
+            traffic = 19.2872 * upd
         roof = {"kernel": names[top], "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_source": peak_kind, "traffic": traffic,
                 "algorithmic_bytes_per_update": alg[names[top]]}
@@ -586,7 +620,8 @@ def main():
                 "data": "synthetic",
                 "config": describe(args.workload, cases, upd, world),
                 "roofline": roof, "kernel_ms": kernel_ms, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clocks}
+                "gpu_launches": launches, "clocks": clocks,
+                "loop": "device-side (conditional while graph)" if args.loop_mode == 0 else "host-launched graphs of 16"}
         print(json.dumps(line), flush=True)
     s.destroy()
     if dist:

@@ -426,6 +426,17 @@ __device__ __forceinline__ P2<T> eq2(const T* q, T ex, T ey, T href, T u, T v, T
     return pfma(pk(H, H * q[E_I2L]), pk(sk, sk + T(2) * L), pk(dH, dB));
 }
 
+// One bulk copy of the per-level batches of k4_cells, formed once per CTA: level l's copy reads src + l sstride
+// and lands in ring slot l & 1 (dst + (l & 1) dslot).  kind 0: a row of the halo rectangle, 1: a row of face
+// parameters (both of level k in batch k), 2: a row of cell coefficients (level k - 1 in batch k); bytes 0: the
+// row lies outside the domain.
+struct alignas(16) K4Copy {
+    const char* src;
+    long long sstride;
+    uint32_t dst, dslot, bytes;
+    int kind;
+};
+
 // Shared-memory layout of k4_cells (byte offsets, pairs for distributions, each block 16-byte aligned):
 //   own   [nt][NCT][32] pairs      the tile's own cells on every level (spectral source, h^k of the update)
 //   rect  [2][NR][32] pairs        per level: the tile with its halo, (TX+3) x (TY+3) cells, two cells on the
@@ -558,6 +569,76 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
         }
     };
     if (warp == 0) issue(0);
+    // the copies of batches 1..nt, formed once: at each level warp 0 then only offsets them
+    constexpr int NQ = PY + 2 * TY + 1 + TY;
+    static_assert(NQ <= 32, "one lane of warp 0 per copy of a batch");
+    __shared__ K4Copy cpy[32];
+    if (warp == 0 && lane < NQ) {
+        K4Copy c;
+        c.bytes = 0;
+        c.src = nullptr;
+        c.sstride = 0;
+        c.dst = 0;
+        c.dslot = 0;
+        c.kind = 0;
+        if (lane < PY) {
+            const int r = lane, jj = j0 + ylo + r;
+            c.kind = 0;
+            if (jj >= 0 && jj < ny) {
+                c.src = reinterpret_cast<const char*>(gf + (size_t)vb * nt * nc * VB + ((size_t)jj * nx + c0) * VB);
+                c.sstride = (long long)nc * VB * sizeof(V);
+                c.dst = smem_u32(rect + (size_t)(r * PX + c0 - (i0 + xlo)) * VB);
+                c.dslot = (uint32_t)(L::RECT * sizeof(V));
+                c.bytes = row_b;
+            }
+        } else if (lane < PY + 2 * TY + 1) {
+            const int r = lane - PY;
+            c.kind = 1;
+            c.sstride = (long long)nf * NP * sizeof(T);
+            c.dslot = (uint32_t)(L::FP * sizeof(T));
+            if (r < TY) {                                     // x-faces of tile row r
+                const int jj = j0 + r;
+                if (jj < ny) {
+                    c.src = reinterpret_cast<const char*>(cd.fpar + ((size_t)jj * (nx + 1) + i0) * NP);
+                    c.dst = smem_u32(fps + (size_t)r * (TX + 1) * NP);
+                    c.bytes = (uint32_t)((nfr + 1) * NP * sizeof(T));
+                }
+            } else {                                          // y-faces of face row r - TY
+                const int fr = r - TY, jj = j0 + fr;
+                if (jj <= jend) {
+                    c.src = reinterpret_cast<const char*>(cd.fpar + ((size_t)nfx + (size_t)jj * nx + i0) * NP);
+                    c.dst = smem_u32(fps + (size_t)(NFX + fr * TX) * NP);
+                    c.bytes = (uint32_t)(nfr * NP * sizeof(T));
+                }
+            }
+        } else {
+            const int r = lane - PY - 2 * TY - 1, jj = j0 + r;  // cells of tile row r
+            c.kind = 2;
+            if (jj < ny) {
+                c.src = reinterpret_cast<const char*>(cd.cpar + ((size_t)jj * nx + i0) * NCP);
+                c.sstride = (long long)nc * NCP * sizeof(T);
+                c.dst = smem_u32(cps + (size_t)r * TX * NCP);
+                c.dslot = (uint32_t)(L::CP * sizeof(T));
+                c.bytes = (uint32_t)(nfr * NCP * sizeof(T));
+            }
+        }
+        cpy[lane] = c;
+    }
+    __syncwarp();
+    // batch k >= 1 (warp 0): rectangle and face parameters of level k (k < nt), cell coefficients of level k - 1
+    auto issue_next = [&](int k) {
+        const bool lvl = k < nt;
+        uint64_t* bar = &bars[k & 1];
+        if (lane == 0) mbar_arrive_expect(bar, (lvl ? rect_b + fp_b : 0u) + cp_b);
+        __syncwarp();
+        if (lane < NQ) {
+            const K4Copy c = cpy[lane];
+            if (c.bytes != 0 && (lvl || c.kind == 2)) {
+                const int l = c.kind == 2 ? k - 1 : k;
+                bulk_g2s_at(c.dst + (uint32_t)(l & 1) * c.dslot, c.src + (long long)l * c.sstride, c.bytes, bar);
+            }
+        }
+    };
     for (int k = threadIdx.x; k < PX; k += blockDim.x) {
         const int ii = i0 + xlo + k;
         gxr[k] = (ii >= 0 && ii < nx - 1) ? T(cd.rdx[ii]) : T(0);
@@ -592,7 +673,7 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
     constexpr bool PAIRED = NCT == 2 * NW;                    // each warp owns two tile cells in pass 1
 
     for (int s = 0; s <= nt; ++s) {
-        if (warp == 0 && s < nt) issue(s + 1);
+        if (warp == 0 && s < nt) issue_next(s + 1);
         // the test hook reports the first wait as expired only after it has completed
         const int fail = !mbar_wait(&bars[s & 1], (uint32_t)((s >> 1) & 1), err) || expire;
         if (__syncthreads_or(fail)) {
