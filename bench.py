@@ -444,6 +444,41 @@ def hb_versus_td(args):
         print(json.dumps(line), flush=True)
 
 
+def batch_versus_single(args, cases):
+    """The cases of a multi-case workload iterated together in one handle, and each case alone in a handle of
+    its own, one after another: device time per iteration (CUDA events, after the warm-up) and updates/s of
+    both ways over the same cases, from rest."""
+    import torch
+    from paper_2605_03479_gb300 import hbugks as hb
+    stream = torch.cuda.current_stream()
+    W_ = max(args.warmup, 3)
+
+    def per_iteration_ms(cs):
+        s = hb.Solver(cs, stream=stream)
+        s.init_uniform(-1, 1.0, 0.0, 0.0, 1.0)
+        s.enqueue_iterations(W_)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.enqueue_iterations(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s.destroy()
+        return e0.elapsed_time(e1) / args.steps
+
+    upd = sum(c.updates_per_iteration() for c in cases)
+    batch_ms = per_iteration_ms(cases)
+    single_ms = [per_iteration_ms([c]) for c in cases]
+    line = {"mode": "batch_vs_single", "workload": args.workload, "cases": len(cases), "steps": args.steps,
+            "warmup": W_, "updates_per_iteration": upd,
+            "batch": {"ms_per_iteration": batch_ms, "updates_per_s": upd / (batch_ms * 1e-3)},
+            "one_by_one": {"ms_per_iteration": sum(single_ms), "updates_per_s": upd / (sum(single_ms) * 1e-3),
+                           "slowest_case_ms": max(single_ms)},
+            "batch_speedup": sum(single_ms) / batch_ms, "data": "synthetic", "start": "rest"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -474,6 +509,8 @@ def main():
                     help="--hb-vs-td: stop each run at the absolute residual (skip the relative drop)")
     ap.add_argument("--spectral-implicit", type=int, default=0,
                     help="--hb-vs-td, --ttr: HB with the spectral source at the new pseudo-time iterate (1)")
+    ap.add_argument("--batch-vs-single", action="store_true",
+                    help="time the workload's cases together in one handle and each alone, one after another")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -488,6 +525,10 @@ def main():
     if args.hb_vs_td > 0:
         if rank == 0:
             hb_versus_td(args)
+        return
+    if args.batch_vs_single:
+        if rank == 0:
+            batch_versus_single(args, cases)
         return
 
     if args.impl == "reference":

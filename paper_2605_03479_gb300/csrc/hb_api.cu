@@ -12,6 +12,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hbugks.h"
 #include "hb_kernels.cuh"
 #include "hb_cells.cuh"
@@ -36,6 +38,16 @@ cudaError_t& last_cuda_error()
 }
 
 constexpr int CHUNK = 16;   // iterations per captured graph
+
+// NVTX range (header-only NVTX 3): a tracing tool attached to the process (Nsight Systems, or any library named
+// by NVTX_INJECTION64_PATH) sees every call of the C ABI, and every kernel stage that an iteration enqueues, as
+// a named range on the calling thread.  With no tool attached a push or pop is one test of a null pointer.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 // timing events destroyed on every return path
 struct Events {
@@ -712,6 +724,8 @@ void enqueue_iteration(Impl<T>& im, int ncases, cudaStream_t s, cudaEvent_t* ev 
             open_slot = slot;
         }
         Batch<T> b{im.d_cases, ncases, im.d_off + (size_t)sp.table * stride};
+        static const char* const names[5] = {"k1_cells", "k2_face_params", "k3_macro", "k_tables", "k4_cells"};
+        Range r(names[sp.kind]);
         switch (sp.kind) {
             case 0: launch_k1<T>(sp.shape, sp.total, sp.smem, b, s); break;
             case 1: k2_face_params<T><<<sp.total, 128, 0, s>>>(b); break;
@@ -724,7 +738,10 @@ void enqueue_iteration(Impl<T>& im, int ncases, cudaStream_t s, cudaEvent_t* ev 
         cudaEventRecord(ev[2 * open_slot + 1], s);
         cudaEventRecord(ev[8], s);
     }
-    k5_finish<T><<<ncases, 32, 0, s>>>(im.d_cases, ncases, im.d_off + (size_t)im.k3_table * stride);
+    {
+        Range r("k5_finish");
+        k5_finish<T><<<ncases, 32, 0, s>>>(im.d_cases, ncases, im.d_off + (size_t)im.k3_table * stride);
+    }
     if (ev) cudaEventRecord(ev[9], s);
 }
 
@@ -1046,6 +1063,7 @@ extern "C" {
 
 size_t hbugks_workspace_bytes(int ncases, const hbugks_case* cases)
 {
+    Range range_("hbugks_workspace_bytes");
     if (ncases < 1 || !cases) return 0;
     for (int k = 0; k < ncases; ++k)
         if (!validate(cases[k]) || cases[k].phys.precision != cases[0].phys.precision) return 0;
@@ -1064,6 +1082,7 @@ size_t hbugks_workspace_bytes(int ncases, const hbugks_case* cases)
 hbugks_status hbugks_create(int ncases, const hbugks_case* cases, void* d_workspace, size_t bytes,
                             void* cuda_stream, hbugks_t* out)
 {
+    Range range_("hbugks_create");
     if (!out || !d_workspace || ((uintptr_t)d_workspace & 255)) return HBUGKS_EINVAL;
     size_t need = hbugks_workspace_bytes(ncases, cases);
     if (need == 0) return HBUGKS_EINVAL;
@@ -1105,6 +1124,7 @@ hbugks_status hbugks_create(int ncases, const hbugks_case* cases, void* d_worksp
 
 void hbugks_destroy(hbugks_t h)
 {
+    Range range_("hbugks_destroy");
     if (!h) return;
     if (h->s) cudaStreamSynchronize(h->s);
     if (h->g1) cudaGraphExecDestroy(h->g1);
@@ -1120,6 +1140,7 @@ void hbugks_destroy(hbugks_t h)
 
 hbugks_status hbugks_set_wall(hbugks_t h, int ci, int wall, const hbugks_wall* w)
 {
+    Range range_("hbugks_set_wall");
     if (!h || !w || ci < 0 || ci >= h->ncases || wall < 0 || wall > 3) return HBUGKS_EINVAL;
     return dispatch(h, [&](auto& im) -> hbugks_status {
         HostCase hc = im.hc[ci];
@@ -1144,6 +1165,7 @@ hbugks_status hbugks_set_wall(hbugks_t h, int ci, int wall, const hbugks_wall* w
 
 hbugks_status hbugks_init_uniform(hbugks_t h, int ci, double rho, double u, double v, double T)
 {
+    Range range_("hbugks_init_uniform");
     if (!h || ci < -1 || ci >= h->ncases || !(rho > 0) || !(T > 0)) return HBUGKS_EINVAL;
     return dispatch(h, [&](auto& im) -> hbugks_status {
         hbugks_status rc = begin(h);
@@ -1163,6 +1185,7 @@ hbugks_status hbugks_init_uniform(hbugks_t h, int ci, double rho, double u, doub
 
 hbugks_status hbugks_set_state(hbugks_t h, int ci, const double* W, const double* hh, const double* bb)
 {
+    Range range_("hbugks_set_state");
     if (!h || ci < 0 || ci >= h->ncases || !W || !hh || !bb) return HBUGKS_EINVAL;
     return dispatch(h, [&](auto& im) -> hbugks_status {
         auto& d = im.dc[ci];
@@ -1187,6 +1210,7 @@ hbugks_status hbugks_set_state(hbugks_t h, int ci, const double* W, const double
 
 hbugks_status hbugks_get_state(hbugks_t h, int ci, double* W, double* hh, double* bb)
 {
+    Range range_("hbugks_get_state");
     if (!h || ci < 0 || ci >= h->ncases || !W || (!hh != !bb)) return HBUGKS_EINVAL;
     return dispatch(h, [&](auto& im) -> hbugks_status {
         auto& d = im.dc[ci];
@@ -1212,6 +1236,7 @@ hbugks_status hbugks_get_state(hbugks_t h, int ci, double* W, double* hh, double
 
 hbugks_status hbugks_set_active(hbugks_t h, const int* flags)
 {
+    Range range_("hbugks_set_active");
     if (!h || !flags) return HBUGKS_EINVAL;
     return dispatch(h, [&](auto& im) -> hbugks_status {
         hbugks_status rc = begin(h);
@@ -1239,6 +1264,7 @@ static hbugks_status launch_iters(hbugks_t h, int n)
 
 hbugks_status hbugks_enqueue_iterations(hbugks_t h, int n)
 {
+    Range range_("hbugks_enqueue_iterations");
     if (!h || n < 0) return HBUGKS_EINVAL;
     return dispatch(h, [&](auto& im) -> hbugks_status {
         hbugks_status rc = begin(h);
@@ -1252,6 +1278,7 @@ hbugks_status hbugks_enqueue_iterations(hbugks_t h, int n)
 
 hbugks_status hbugks_iterate(hbugks_t h, int max_iters, double tol_rho, int* iters_done, double* resid_out)
 {
+    Range range_("hbugks_iterate");
     if (!h || max_iters < 0) return HBUGKS_EINVAL;
     return dispatch(h, [&](auto& im) -> hbugks_status {
         hbugks_status rc = begin(h);
@@ -1314,6 +1341,7 @@ hbugks_status hbugks_iterate(hbugks_t h, int max_iters, double tol_rho, int* ite
 
 hbugks_status hbugks_residual_history(hbugks_t h, int ci, int n, double* out)
 {
+    Range range_("hbugks_residual_history");
     if (!h || ci < 0 || ci >= h->ncases || n < 0 || n > RING || !out) return HBUGKS_EINVAL;
     return dispatch(h, [&](auto& im) -> hbugks_status {
         hbugks_status rc = begin(h);
@@ -1334,6 +1362,7 @@ hbugks_status hbugks_residual_history(hbugks_t h, int ci, int n, double* out)
 
 hbugks_status hbugks_get_level_fields(hbugks_t h, int ci, int level, double* out)
 {
+    Range range_("hbugks_get_level_fields");
     if (!h || ci < 0 || ci >= h->ncases || !out) return HBUGKS_EINVAL;
     return dispatch(h, [&](auto& im) -> hbugks_status {
         auto& d = im.dc[ci];
@@ -1350,6 +1379,7 @@ hbugks_status hbugks_get_level_fields(hbugks_t h, int ci, int level, double* out
 
 hbugks_status hbugks_get_harmonic(hbugks_t h, int ci, int k, double* re, double* im_out)
 {
+    Range range_("hbugks_get_harmonic");
     if (!h || ci < 0 || ci >= h->ncases || !re || !im_out) return HBUGKS_EINVAL;
     return dispatch(h, [&](auto& im) -> hbugks_status {
         auto& d = im.dc[ci];
@@ -1383,6 +1413,7 @@ long long hbugks_iteration_count(hbugks_t h, int ci)
 
 hbugks_status hbugks_profile_kernels(hbugks_t h, int n, double* ms)
 {
+    Range range_("hbugks_profile_kernels");
     if (!h || n < 1 || !ms) return HBUGKS_EINVAL;
     return dispatch(h, [&](auto& im) -> hbugks_status {
         hbugks_status rc = begin(h);
@@ -1411,6 +1442,7 @@ hbugks_status hbugks_harmonic_noalloc(int nx, int ny, int nu, int nv, const doub
                                       const double* wv, int nt, const double* h, const double* b, int k, double* re,
                                       double* im, void* cuda_stream)
 {
+    Range range_("hbugks_harmonic_noalloc");
     if (nx < 1 || ny < 1 || nu < 1 || nv < 1 || nt < 1 || !(nt & 1) || !u || !wu || !v || !wv || !h || !b || !re || !im)
         return HBUGKS_EINVAL;
     if (k < 0 || k > (nt - 1) / 2) return HBUGKS_EINVAL;
@@ -1430,6 +1462,7 @@ hbugks_status hbugks_harmonic_noalloc(int nx, int ny, int nu, int nv, const doub
 
 hbugks_status hbugks_copy_state(hbugks_t dst, int dst_case, hbugks_t src, int src_case)
 {
+    Range range_("hbugks_copy_state");
     if (!dst || !src || dst == src || dst_case < 0 || dst_case >= dst->ncases || src_case < 0 ||
         src_case >= src->ncases)
         return HBUGKS_EINVAL;
@@ -1467,6 +1500,7 @@ hbugks_status hbugks_copy_state(hbugks_t dst, int dst_case, hbugks_t src, int sr
 
 hbugks_status hbugks_test_expire_wait(hbugks_t h)
 {
+    Range range_("hbugks_test_expire_wait");
     if (!h) return HBUGKS_EINVAL;
     return dispatch(h, [&](auto& im) -> hbugks_status {
         hbugks_status rc = begin(h);
@@ -1489,6 +1523,7 @@ hbugks_status hbugks_get_tile_shape(hbugks_t h, int case_index, int* tx, int* ty
 
 hbugks_status hbugks_set_tile_shape(hbugks_t h, int case_index, int tx, int ty)
 {
+    Range range_("hbugks_set_tile_shape");
     if (!h || case_index < 0 || case_index >= h->ncases) return HBUGKS_EINVAL;
     int sh = -1;
     for (int k = 0; k < N_K4_SHAPES; ++k)
@@ -1525,6 +1560,7 @@ int hbugks_launches_per_iteration(hbugks_t h)
 
 hbugks_status hbugks_set_loop_mode(hbugks_t h, int mode)
 {
+    Range range_("hbugks_set_loop_mode");
     if (!h || (mode != 0 && mode != 1)) return HBUGKS_EINVAL;
     h->loop_mode = mode;
     return HBUGKS_OK;

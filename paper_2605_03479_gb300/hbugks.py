@@ -168,7 +168,9 @@ def workspace_bytes(cases: Sequence) -> int:
 class Solver:
     """A handle over one or more cavity cases (a batch), with its device workspace owned by a torch tensor."""
 
-    def __init__(self, cases, device: str = "cuda:0", stream=None):
+    def __init__(self, cases, device: str = "cuda:0", stream=None, workspace_fill: int | None = None):
+        """workspace_fill: a byte value written over the whole workspace before the handle is created (the
+        tests fill it with 0xFF, NaN in both precisions, to show that nothing reads memory it has not written)."""
         import torch
         if not isinstance(cases, (list, tuple)):
             cases = [cases]
@@ -180,6 +182,9 @@ class Solver:
             raise HbugksError(EINVAL, "hbugks_workspace_bytes")
         self.device = torch.device(device)
         self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        if workspace_fill is not None:
+            self.workspace.fill_(int(workspace_fill))
+            torch.cuda.synchronize(self.device)
         base = self.workspace.data_ptr()
         aligned = (base + 255) // 256 * 256
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
