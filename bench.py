@@ -30,6 +30,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "HB-UGKS cell*velocity*level updates/s"
+# ncu DRAM bytes (read + write) per update of one k4_cells launch on the 64x64-cell, 64x64-velocity, N_T = 11
+# thermal cavity, by micro-update variant (tile x, tile y, velocity blocks per CTA); see profiles/
+K4_TRAFFIC_64 = {}
 UNIT = "updates/s"
 
 
@@ -509,6 +512,8 @@ def main():
                     help="--hb-vs-td: stop each run at the absolute residual (skip the relative drop)")
     ap.add_argument("--spectral-implicit", type=int, default=0,
                     help="--hb-vs-td, --ttr: HB with the spectral source at the new pseudo-time iterate (1)")
+    ap.add_argument("--micro-variant", default=None,
+                    help="pin every case's micro-update variant, 'tx,ty,vpl' (default: the autotuner's choice)")
     ap.add_argument("--batch-vs-single", action="store_true",
                     help="time the workload's cases together in one handle and each alone, one after another")
     args = ap.parse_args()
@@ -562,6 +567,10 @@ def main():
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     s = hb.Solver(cases, device=dev, stream=stream)
+    if args.micro_variant:
+        mv = [int(x) for x in args.micro_variant.split(",")]
+        for k in range(len(cases)):
+            s.set_micro_variant(k, *mv)
     s.set_loop_mode(args.loop_mode)
     s.init_uniform(-1, 1.0, 0.0, 0.0, 1.0)
     s.enqueue_iterations(W_)
@@ -600,14 +609,15 @@ def main():
     if names[top] in alg:
         ach = alg[names[top]] * upd / (kms[top] * 1e-3) / 1e9
         # DRAM bytes per update of the micro update (dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-        # launch of k4_cells<float, 4, 4, 8> on the 64x64-cell thermal cavity with the 64x64 velocity grid and
-        # N_T = 11: 3.5594 GB for 184.5 M updates), scaled by updates; only where the launches match that
-        # capture: 4x4 tiles, the 64x64 velocity grid, N_T = 11
+        # launch of k4_cells on the 64x64-cell thermal cavity with the 64x64 velocity grid and N_T = 11, per
+        # micro-update variant), scaled by updates; only where the launches match that capture: the same
+        # variant, the 64x64 velocity grid, N_T = 11
         traffic = None
-        if names[top] == "micro_update" and case.precision == 1 and all(
-                s.tile_shape(k) == (4, 4) and c.nu == 64 and c.nv == 64 and c.nt == 11
-                for k, c in enumerate(cases)):
-            traffic = 19.2872 * upd
+        variants = {s.micro_variant(k) for k in range(len(cases))}
+        if names[top] == "micro_update" and case.precision == 1 and len(variants) == 1 and all(
+                c.nu == 64 and c.nv == 64 and c.nt == 11 for c in cases):
+            per_update = K4_TRAFFIC_64.get(next(iter(variants)))
+            traffic = per_update * upd if per_update else None
         roof = {"kernel": names[top], "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_source": peak_kind, "traffic": traffic,
                 "algorithmic_bytes_per_update": alg[names[top]]}
@@ -660,7 +670,9 @@ def main():
                 "vs_baseline": None, "dtype": "f32-split" if case.precision == 1 else "f64",
                 "data": "synthetic",
                 "config": describe(args.workload, cases, upd, world),
-                "roofline": roof, "kernel_ms": kernel_ms, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "kernel_ms": kernel_ms,
+                "micro_variants": sorted({s.micro_variant(k) for k in range(len(cases))}),
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks,
                 "loop": "device-side (conditional while graph)" if args.loop_mode == 0 else "host-launched graphs of 16"}
         print(json.dumps(line), flush=True)

@@ -211,13 +211,19 @@ HBUGKS_API hbugks_status hbugks_harmonic_noalloc(int nx, int ny, int nu, int nv,
                                                  const double* v, const double* wv, int nt, const double* h,
                                                  const double* b, int k, double* re, double* im, void* cuda_stream);
 
-/* Tile of the micro-update kernel (cells along x and y handled by one CTA, all levels of one block of 32
- * velocities).  hbugks_create() picks it per case by timing every tile that fits in shared memory on the case
- * itself (autotuning, cached per process by mesh size, velocity grid, level count, precision and SM count).
- * get: the tile of case `case_index`.  set: pin a tile (4x4, 4x2, 2x2 or 8x4), for example to reproduce a run
- * exactly; HBUGKS_EINVAL if the tile is not one of these or needs more shared memory than a CTA may have.
- * The state is unchanged; the iteration graphs are rebuilt.  The paper has no counterpart (a GPU tuning
- * choice). */
+/* Variant of the micro-update kernel of a case: its tile (tx x ty cells per CTA, all levels) and vpl, the
+ * blocks of 32 velocities per CTA (1, or 2: each lane then updates one velocity of each of two blocks of the
+ * same sign class, sharing the per-cell and per-face indices and parameters between them).  The variants are
+ * 4x4, 4x2, 2x2 and 8x4 with vpl 1, and 4x2 with vpl 2, which needs single precision and sign classes that
+ * each hold an even number of velocity blocks.  hbugks_create() picks one per case by timing every variant the
+ * case can run on the case itself (autotuning, cached per process by mesh size, velocity grid, level count,
+ * precision and SM count).  get: the variant of case `case_index`.  set: pin one, for example to reproduce a
+ * run exactly; HBUGKS_EINVAL if it is not one of these, needs more shared memory than a CTA may have, or needs
+ * what the case lacks.  Every variant gives bitwise the same iterate; the state is unchanged and the iteration
+ * graphs are rebuilt.  The tile-shape pair is the same with vpl = 1 (set) or any vpl (get).  The paper has no
+ * counterpart (a GPU tuning choice). */
+HBUGKS_API hbugks_status hbugks_get_micro_variant(hbugks_t h, int case_index, int* tx, int* ty, int* vpl);
+HBUGKS_API hbugks_status hbugks_set_micro_variant(hbugks_t h, int case_index, int tx, int ty, int vpl);
 HBUGKS_API hbugks_status hbugks_get_tile_shape(hbugks_t h, int case_index, int* tx, int* ty);
 HBUGKS_API hbugks_status hbugks_set_tile_shape(hbugks_t h, int case_index, int tx, int ty);
 

@@ -98,6 +98,7 @@ struct HostCase {
     int k1b, k2b, k3b, k4b, ksb, ktb;
     int k4shape;
     int k1sep;                      // face sums by v-moments: no zero node, every sign class 1..32 u-nodes wide
+    int pairs;                      // every sign class holds an even number of velocity blocks
 };
 
 // K1 tile (TX x TY cells, one warp each) and velocity blocks staged per pass, per storage precision
@@ -118,20 +119,23 @@ constexpr auto k1_kernel()
 }
 
 // K4 tile shapes (TX, TY, warps per CTA)
+// K4 variants: tile (TX, TY), warps per CTA, velocity blocks per CTA (2: single precision only, and only for
+// cases whose sign classes each hold an even number of blocks)
 struct Shape {
-    int tx, ty, nw;
+    int tx, ty, nw, vpl;
 };
-constexpr Shape K4_SHAPES[] = {{4, 4, 8}, {4, 2, 8}, {2, 2, 4}, {8, 4, 16}};
-constexpr int N_K4_SHAPES = 4;
+constexpr Shape K4_SHAPES[] = {{4, 4, 8, 1}, {4, 2, 8, 1}, {2, 2, 4, 1}, {8, 4, 16, 1}, {4, 2, 8, 2}};
+constexpr int N_K4_SHAPES = 5;
 
 template <typename T>
 size_t k4_smem_of(int shape, int nt)
 {
     switch (shape) {
-        case 0: return k4_cells_smem<T, 4, 4>(nt);
-        case 1: return k4_cells_smem<T, 4, 2>(nt);
-        case 2: return k4_cells_smem<T, 2, 2>(nt);
-        default: return k4_cells_smem<T, 8, 4>(nt);
+        case 0: return k4_cells_smem<T, 4, 4, 1>(nt);
+        case 1: return k4_cells_smem<T, 4, 2, 1>(nt);
+        case 2: return k4_cells_smem<T, 2, 2, 1>(nt);
+        case 3: return k4_cells_smem<T, 8, 4, 1>(nt);
+        default: return k4_cells_smem<T, 4, 2, 2>(nt);
     }
 }
 
@@ -142,10 +146,19 @@ template <typename T>
 int pick_k4_shape(int nt)
 {
     for (int s = 0; s < N_K4_SHAPES; ++s)
-        if (k4_smem_of<T>(s, nt) <= 113 * 1024) return s;
+        if (K4_SHAPES[s].vpl == 1 && k4_smem_of<T>(s, nt) <= 113 * 1024) return s;
     for (int s = 0; s < N_K4_SHAPES; ++s)
-        if (k4_smem_of<T>(s, nt) <= SMEM_MAX) return s;
+        if (K4_SHAPES[s].vpl == 1 && k4_smem_of<T>(s, nt) <= SMEM_MAX) return s;
     return -1;
+}
+
+// a K4 variant a case of this precision can run: its shared memory fits a CTA, and two velocity blocks per
+// CTA need single precision and sign classes of an even number of blocks (the CTA's blocks share one class)
+template <typename T>
+bool k4_shape_ok(int shape, int nt, bool pairs)
+{
+    if (shape < 0 || shape >= N_K4_SHAPES || k4_smem_of<T>(shape, nt) > SMEM_MAX) return false;
+    return K4_SHAPES[shape].vpl == 1 || (sizeof(T) == 4 && pairs);
 }
 
 // finite and strictly positive
@@ -211,6 +224,11 @@ void fill_host(HostCase& h, const hbugks_case& c)
     }
     h.nvp = (int)h.vcan.size();
     h.nvb = h.nvp / VB;
+    {
+        int cnt[4] = {0, 0, 0, 0};
+        for (int c : h.vcls) ++cnt[c];
+        h.pairs = cnt[0] % 2 == 0 && cnt[1] % 2 == 0 && cnt[2] % 2 == 0 && cnt[3] % 2 == 0;
+    }
     {
         int upos = 0, uneg = 0, zero = 0;
         for (int iu = 0; iu < h.nu; ++iu) {
@@ -376,7 +394,7 @@ void set_k4_blocks(HostCase& h)
 {
     if (h.k4shape < 0) { h.k4b = 0; return; }
     const Shape s4 = K4_SHAPES[h.k4shape];
-    h.k4b = ((h.nx + s4.tx - 1) / s4.tx) * ((h.ny + s4.ty - 1) / s4.ty) * h.nvb;
+    h.k4b = ((h.nx + s4.tx - 1) / s4.tx) * ((h.ny + s4.ty - 1) / s4.ty) * (h.nvb / s4.vpl);
 }
 
 template <typename T>
@@ -670,10 +688,13 @@ template <typename T, bool IMP>
 void launch_k4_(int shape, int total, size_t smem, Batch<T> b, cudaStream_t s)
 {
     switch (shape) {
-        case 0: k4_cells<T, 4, 4, 8, IMP><<<total, 8 * 32, smem, s>>>(b); break;
-        case 1: k4_cells<T, 4, 2, 8, IMP><<<total, 8 * 32, smem, s>>>(b); break;
-        case 2: k4_cells<T, 2, 2, 4, IMP><<<total, 4 * 32, smem, s>>>(b); break;
-        default: k4_cells<T, 8, 4, 16, IMP><<<total, 16 * 32, smem, s>>>(b); break;
+        case 0: k4_cells<T, 4, 4, 8, IMP, 1><<<total, 8 * 32, smem, s>>>(b); break;
+        case 1: k4_cells<T, 4, 2, 8, IMP, 1><<<total, 8 * 32, smem, s>>>(b); break;
+        case 2: k4_cells<T, 2, 2, 4, IMP, 1><<<total, 4 * 32, smem, s>>>(b); break;
+        case 3: k4_cells<T, 8, 4, 16, IMP, 1><<<total, 16 * 32, smem, s>>>(b); break;
+        default:
+            if constexpr (sizeof(T) == 4) k4_cells<T, 4, 2, 8, IMP, 2><<<total, 8 * 32, smem, s>>>(b);
+            break;
     }
 }
 
@@ -698,10 +719,14 @@ cudaError_t set_smem_attributes()
     auto set = [&](auto k) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     };
-    set(k4_cells<T, 4, 4, 8, false>); set(k4_cells<T, 4, 2, 8, false>);
-    set(k4_cells<T, 2, 2, 4, false>); set(k4_cells<T, 8, 4, 16, false>);
-    set(k4_cells<T, 4, 4, 8, true>); set(k4_cells<T, 4, 2, 8, true>);
-    set(k4_cells<T, 2, 2, 4, true>); set(k4_cells<T, 8, 4, 16, true>);
+    set(k4_cells<T, 4, 4, 8, false, 1>); set(k4_cells<T, 4, 2, 8, false, 1>);
+    set(k4_cells<T, 2, 2, 4, false, 1>); set(k4_cells<T, 8, 4, 16, false, 1>);
+    set(k4_cells<T, 4, 4, 8, true, 1>); set(k4_cells<T, 4, 2, 8, true, 1>);
+    set(k4_cells<T, 2, 2, 4, true, 1>); set(k4_cells<T, 8, 4, 16, true, 1>);
+    if constexpr (sizeof(T) == 4) {
+        set(k4_cells<T, 4, 2, 8, false, 2>);
+        set(k4_cells<T, 4, 2, 8, true, 2>);
+    }
     return e;
 }
 
@@ -887,10 +912,10 @@ hbugks_status autotune(hbugks_t h, Impl<T>& im, int ncases)
             int best = -1;
             float best_ms = 0.f;
             for (int sh = 0; sh < N_K4_SHAPES; ++sh) {
+                if (!k4_shape_ok<T>(sh, hc.nt, hc.pairs != 0)) continue;
                 const size_t smem = k4_smem_of<T>(sh, hc.nt);
-                if (smem > SMEM_MAX) continue;
                 const Shape S = K4_SHAPES[sh];
-                const int off[2] = {0, ((hc.nx + S.tx - 1) / S.tx) * ((hc.ny + S.ty - 1) / S.ty) * hc.nvb};
+                const int off[2] = {0, ((hc.nx + S.tx - 1) / S.tx) * ((hc.ny + S.ty - 1) / S.ty) * (hc.nvb / S.vpl)};
                 HB_CK(cudaMemcpyAsync(im.d_tune_off, off, sizeof off, cudaMemcpyHostToDevice, h->s));
                 const Batch<T> b{im.d_cases + k, 1, im.d_tune_off};
                 const bool imp = hc.src.phys.spectral_implicit != 0;
@@ -1512,27 +1537,28 @@ hbugks_status hbugks_test_expire_wait(hbugks_t h)
     });
 }
 
-hbugks_status hbugks_get_tile_shape(hbugks_t h, int case_index, int* tx, int* ty)
+hbugks_status hbugks_get_micro_variant(hbugks_t h, int case_index, int* tx, int* ty, int* vpl)
 {
-    if (!h || case_index < 0 || case_index >= h->ncases || !tx || !ty) return HBUGKS_EINVAL;
+    if (!h || case_index < 0 || case_index >= h->ncases || !tx || !ty || !vpl) return HBUGKS_EINVAL;
     const int sh = dispatch(h, [&](auto& im) { return im.hc[case_index].k4shape; });
     *tx = K4_SHAPES[sh].tx;
     *ty = K4_SHAPES[sh].ty;
+    *vpl = K4_SHAPES[sh].vpl;
     return HBUGKS_OK;
 }
 
-hbugks_status hbugks_set_tile_shape(hbugks_t h, int case_index, int tx, int ty)
+hbugks_status hbugks_set_micro_variant(hbugks_t h, int case_index, int tx, int ty, int vpl)
 {
-    Range range_("hbugks_set_tile_shape");
+    Range range_("hbugks_set_micro_variant");
     if (!h || case_index < 0 || case_index >= h->ncases) return HBUGKS_EINVAL;
     int sh = -1;
     for (int k = 0; k < N_K4_SHAPES; ++k)
-        if (K4_SHAPES[k].tx == tx && K4_SHAPES[k].ty == ty) sh = k;
+        if (K4_SHAPES[k].tx == tx && K4_SHAPES[k].ty == ty && K4_SHAPES[k].vpl == vpl) sh = k;
     if (sh < 0) return HBUGKS_EINVAL;
     return dispatch(h, [&](auto& im) -> hbugks_status {
         using T = typename std::remove_reference<decltype(*im.d_cases)>::type::value_type;
         HostCase& hc = im.hc[case_index];
-        if (k4_smem_of<T>(sh, hc.nt) > SMEM_MAX) return HBUGKS_EINVAL;
+        if (!k4_shape_ok<T>(sh, hc.nt, hc.pairs != 0)) return HBUGKS_EINVAL;
         hbugks_status rc = begin(h);
         if (rc) return rc;
         hc.k4shape = sh;
@@ -1545,6 +1571,17 @@ hbugks_status hbugks_set_tile_shape(hbugks_t h, int case_index, int tx, int ty)
         if ((rc = capture(h, im)) != HBUGKS_OK) return rc;
         return end(h);
     });
+}
+
+hbugks_status hbugks_get_tile_shape(hbugks_t h, int case_index, int* tx, int* ty)
+{
+    int vpl = 0;
+    return hbugks_get_micro_variant(h, case_index, tx, ty, &vpl);
+}
+
+hbugks_status hbugks_set_tile_shape(hbugks_t h, int case_index, int tx, int ty)
+{
+    return hbugks_set_micro_variant(h, case_index, tx, ty, 1);
 }
 
 int hbugks_launches_per_iteration(hbugks_t h)

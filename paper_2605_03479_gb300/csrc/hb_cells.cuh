@@ -10,11 +10,12 @@
 //   k4_cells : per (cell, level, 32 velocities): interface micro fluxes (Eq. micro_flux), spectral source and
 //              the semi-implicit collision update (Eq. fv_h).
 // A CTA of k1_cells owns a tile of cells and one level and runs over all velocity blocks; a CTA of k4_cells
-// owns a tile of cells and one velocity block and runs over all levels.  Both stage the tile and its halo in
-// shared memory with bulk copies (TMA) completing on an mbarrier.  The distributions h and b of a velocity are
-// stored side by side and carried as one pair (hb_common.cuh): one 8-byte access and, in single precision, one
-// packed FP32x2 instruction for both wherever they see the same arithmetic (differences, limited slopes,
-// reconstruction, the flux combination, spectral source and update).
+// owns a tile of cells and one or two velocity blocks of one sign class and runs over all levels.  Both stage
+// the tile and its halo in shared memory with bulk copies (TMA) completing on an mbarrier.  The distributions
+// h and b of a velocity are stored side by side and carried as one pair (hb_common.cuh): one 8-byte access
+// and, in single precision, one packed FP32x2 instruction for both wherever they see the same arithmetic
+// (differences, limited slopes, reconstruction, the flux combination, velocity sums with a common weight,
+// spectral source and update).
 #pragma once
 #include "hb_common.cuh"
 
@@ -72,6 +73,26 @@ __device__ __forceinline__ V spectral2(const V* fc, int n, int nt, int lv, const
         e = pfma(etb[d], psub(fc[nm * lv], fc[np * lv]), e);
     }
     return e;
+}
+
+// spectral source of every level of one cell and lane, in place: the pair of level n (levels lv pairs apart)
+// becomes sum_d e_d (f_{n-d} - f_{n+d}), with the operations of spectral2 in the same order
+template <int NH, typename V, typename T>
+__device__ __forceinline__ void spectral_all(V* fc, int lv, const T* et)
+{
+    constexpr int NT = 2 * NH + 1;
+    V f[NT], eb[NH + 1];
+#pragma unroll
+    for (int m = 0; m < NT; ++m) f[m] = fc[m * lv];
+#pragma unroll
+    for (int d = 0; d <= NH; ++d) eb[d] = bc(et[d]);
+#pragma unroll
+    for (int n = 0; n < NT; ++n) {
+        V e = eb[0];
+#pragma unroll
+        for (int d = 1; d <= NH; ++d) e = pfma(eb[d], psub(f[(n - d + NT) % NT], f[(n + d) % NT]), e);
+        fc[n * lv] = e;
+    }
 }
 
 __device__ __forceinline__ void mbar_setup(uint64_t* bars, int n)
@@ -201,17 +222,47 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
 
     // general: the 23 + 23 + 13 sums per lane; SEP: v-moments per lane (x-face h: 4, b: 2, tangential h: 3,
     // b: 1, normal-flux h: 3, b: 1; the y-face alike; cell h: 4, b: 2), folded into the 23 + 23 + 13 at a
-    // class change
-    constexpr int NA = SEP ? 14 : NM, NC = SEP ? 6 : NCM;
-    T ax[NA], ay[NA], cc[NC], ac[NCM];
+    // class change.  A sum of h and the sum of b with the same weight are kept as one pair (one packed FMA):
+    //   SEP      xp: (0, 4) (1, 5) (6, 9) (10, 13) of the 14 v-moments, xs: 2 3 7 8 11 12;  cp: (0, 4) (1, 5),
+    //            csm: 2 3 of the 6 cell v-moments
+    //   general  xp: (0, 10) (1, 11) (2, 12) (13, 17) (18, 22) of the 23 sums, xs: 3..9, 14..16, 19..21;
+    //            cp: (0, 10) (1, 11) (2, 12), csm: 3..9 of the 13 cell sums
+    constexpr int NXP = SEP ? 4 : 5, NXS = SEP ? 6 : 13, NCP2 = SEP ? 2 : 3, NCS = SEP ? 2 : 7;
+    V xp[NXP], yp[NXP], cp2[NCP2];
+    T xs[NXS], ys[NXS], csm[NCS], ac[NCM];
+    auto zero_faces = [&]() {
 #pragma unroll
-    for (int q = 0; q < NA; ++q) { ax[q] = T(0); ay[q] = T(0); }
+        for (int q = 0; q < NXP; ++q) { xp[q] = bc(T(0)); yp[q] = bc(T(0)); }
 #pragma unroll
-    for (int q = 0; q < NC; ++q) cc[q] = T(0);
+        for (int q = 0; q < NXS; ++q) { xs[q] = T(0); ys[q] = T(0); }
+    };
+    auto zero_cell = [&]() {
+#pragma unroll
+        for (int q = 0; q < NCP2; ++q) cp2[q] = bc(T(0));
+#pragma unroll
+        for (int q = 0; q < NCS; ++q) csm[q] = T(0);
+    };
+    zero_faces();
+    zero_cell();
 #pragma unroll
     for (int q = 0; q < NCM; ++q) ac[q] = T(0);
     int cur = -1;
     T ul = T(0), wul = T(0);                                 // SEP: the lane's u and w_u in the current class
+    // the 14 v-moments of a face (SEP) or its 23 sums (general) in slot order
+    auto face_sums = [&](const V (&P)[NXP], const T (&S_)[NXS], T (&m)[SEP ? 14 : NM]) {
+        if constexpr (SEP) {
+            m[0] = P[0].x; m[1] = P[1].x; m[2] = S_[0]; m[3] = S_[1]; m[4] = P[0].y; m[5] = P[1].y;
+            m[6] = P[2].x; m[7] = S_[2]; m[8] = S_[3]; m[9] = P[2].y; m[10] = P[3].x; m[11] = S_[4];
+            m[12] = S_[5]; m[13] = P[3].y;
+        } else {
+            m[0] = P[0].x; m[1] = P[1].x; m[2] = P[2].x;
+#pragma unroll
+            for (int q = 0; q < 7; ++q) m[3 + q] = S_[q];
+            m[10] = P[0].y; m[11] = P[1].y; m[12] = P[2].y; m[13] = P[3].x;
+            m[14] = S_[7]; m[15] = S_[8]; m[16] = S_[9]; m[17] = P[3].y; m[18] = P[4].x;
+            m[19] = S_[10]; m[20] = S_[11]; m[21] = S_[12]; m[22] = P[4].y;
+        }
+    };
     // the 23 face sums of one face from its v-moments m (SEP)
     auto unfold = [&](const T (&m)[14], T (&o)[NM]) {
         const T w1 = wul, w2 = w1 * ul, w3 = w2 * ul, w4 = w3 * ul;     // w_u u^a
@@ -227,28 +278,32 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
     auto flush = [&]() {
         T tx_, ty_;
         if constexpr (SEP) {
-            T ox[NM], oy[NM];
-            unfold(ax, ox);
-            unfold(ay, oy);
+            T mx[14], my[14], ox[NM], oy[NM];
+            face_sums(xp, xs, mx);
+            face_sums(yp, ys, my);
+            unfold(mx, ox);
+            unfold(my, oy);
+            const T c0 = cp2[0].x, c1 = cp2[1].x, c2 = csm[0], c3 = csm[1], c4 = cp2[0].y, c5 = cp2[1].y;
             const T w1 = wul, w2 = w1 * ul, w3 = w2 * ul, w4 = w3 * ul;
-            ac[0] += w1 * cc[0]; ac[1] += w2 * cc[0]; ac[2] += w1 * cc[1]; ac[3] += w3 * cc[0];
-            ac[4] += w2 * cc[1]; ac[5] += w1 * cc[2]; ac[6] += w4 * cc[0]; ac[7] += w3 * cc[1];
-            ac[8] += w2 * cc[2]; ac[9] += w1 * cc[3];
-            ac[10] += w1 * cc[4]; ac[11] += w2 * cc[4]; ac[12] += w1 * cc[5];
-#pragma unroll
-            for (int q = 0; q < NC; ++q) cc[q] = T(0);
+            ac[0] += w1 * c0; ac[1] += w2 * c0; ac[2] += w1 * c1; ac[3] += w3 * c0;
+            ac[4] += w2 * c1; ac[5] += w1 * c2; ac[6] += w4 * c0; ac[7] += w3 * c1;
+            ac[8] += w2 * c2; ac[9] += w1 * c3;
+            ac[10] += w1 * c4; ac[11] += w2 * c4; ac[12] += w1 * c5;
+            zero_cell();
             tx_ = lane_totals<NM>(ox, lane);
             ty_ = lane_totals<NM>(oy, lane);
         } else {
-            tx_ = lane_totals<NM>(ax, lane);
-            ty_ = lane_totals<NM>(ay, lane);
+            T ox[NM], oy[NM];
+            face_sums(xp, xs, ox);
+            face_sums(yp, ys, oy);
+            tx_ = lane_totals<NM>(ox, lane);
+            ty_ = lane_totals<NM>(oy, lane);
         }
         if (lane < NM) {
             sacc[warp][(cur & 1) ? 1 : 0][lane] += tx_;
             sacc[warp][(cur & 2) ? 3 : 2][lane] += ty_;
         }
-#pragma unroll
-        for (int q = 0; q < NA; ++q) { ax[q] = T(0); ay[q] = T(0); }
+        zero_faces();
     };
 
     // Ring of S slots: chunk k lands in slot k % S (mbarrier bars); each warp arrives on empty once it has
@@ -308,47 +363,47 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
                     if ((xn ? !hm : !hp) && u == T(0)) dx = bc(T(0));
                     if ((yn ? !vm : !vp) && v == T(0)) dy = bc(T(0));
                 }
-                const T sxh = sxv.x, sxb = sxv.y, syh = syv.x, syb = syv.y;
+                const T sxh = sxv.x, syh = syv.x;
                 if constexpr (SEP) {
                     // w is w_v here; v-moments of every summand
                     const T c1 = w * v, c2 = c1 * v, c3 = c2 * v;
-                    const T txh = ul * (ul * sxh + v * syh), tyh = v * (v * syh + ul * sxh);
-                    const T txb = ul * (ul * sxb + v * syb), tyb = v * (v * syb + ul * sxb);
-                    ax[0] += dx.x * w; ax[1] += dx.x * c1; ax[2] += dx.x * c2; ax[3] += dx.x * c3;
-                    ay[0] += dy.x * w; ay[1] += dy.x * c1; ay[2] += dy.x * c2; ay[3] += dy.x * c3;
-                    ax[4] += dx.y * w; ax[5] += dx.y * c1;
-                    ay[4] += dy.y * w; ay[5] += dy.y * c1;
-                    ax[6] += syh * w; ax[7] += syh * c1; ax[8] += syh * c2; ax[9] += syb * w;
-                    ay[6] += sxh * w; ay[7] += sxh * c1; ay[8] += sxh * c2; ay[9] += sxb * w;
-                    ax[10] += txh * w; ax[11] += txh * c1; ax[12] += txh * c2; ax[13] += txb * w;
-                    ay[10] += tyh * w; ay[11] += tyh * c1; ay[12] += tyh * c2; ay[13] += tyb * w;
-                    cc[0] += f0.x * w; cc[1] += f0.x * c1; cc[2] += f0.x * c2; cc[3] += f0.x * c3;
-                    cc[4] += f0.y * w; cc[5] += f0.y * c1;
+                    const V bw = bc(w), bc1 = bc(c1);
+                    const V tx = pmul(bc(ul), pfma(bc(ul), sxv, pmul(bc(v), syv)));   // u_n (u_n s_n + u_t s_t)
+                    const V ty = pmul(bc(v), pfma(bc(v), syv, pmul(bc(ul), sxv)));
+                    xp[0] = pfma(dx, bw, xp[0]); xp[1] = pfma(dx, bc1, xp[1]);
+                    xs[0] += dx.x * c2; xs[1] += dx.x * c3;
+                    yp[0] = pfma(dy, bw, yp[0]); yp[1] = pfma(dy, bc1, yp[1]);
+                    ys[0] += dy.x * c2; ys[1] += dy.x * c3;
+                    xp[2] = pfma(syv, bw, xp[2]); xs[2] += syh * c1; xs[3] += syh * c2;
+                    yp[2] = pfma(sxv, bw, yp[2]); ys[2] += sxh * c1; ys[3] += sxh * c2;
+                    xp[3] = pfma(tx, bw, xp[3]); xs[4] += tx.x * c1; xs[5] += tx.x * c2;
+                    yp[3] = pfma(ty, bw, yp[3]); ys[4] += ty.x * c1; ys[5] += ty.x * c2;
+                    cp2[0] = pfma(f0, bw, cp2[0]); cp2[1] = pfma(f0, bc1, cp2[1]);
+                    csm[0] += f0.x * c2; csm[1] += f0.x * c3;
                     continue;
                 }
                 if constexpr (!SEP) {
                     const T wu = w * u, wv = w * v, wuu = wu * u, wuv = wu * v, wvv = wv * v;
                     const T m[10] = {w, wu, wv, wuu, wuv, wvv, wuu * u, wuu * v, wvv * u, wvv * v};
                     const T wq = wuu + wvv;
-#pragma unroll
-                    for (int q = 0; q < 10; ++q) {
-                        ax[q] += dx.x * m[q];
-                        ay[q] += dy.x * m[q];
-                        ac[q] += f0.x * m[q];
-                    }
+                    const V tx = pmul(bc(u), pfma(bc(u), sxv, pmul(bc(v), syv)));
+                    const V ty = pmul(bc(v), pfma(bc(v), syv, pmul(bc(u), sxv)));
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
-                        ax[10 + q] += dx.y * m[q];
-                        ay[10 + q] += dy.y * m[q];
-                        ac[10 + q] += f0.y * m[q];
+                        xp[q] = pfma(dx, bc(m[q]), xp[q]);
+                        yp[q] = pfma(dy, bc(m[q]), yp[q]);
+                        cp2[q] = pfma(f0, bc(m[q]), cp2[q]);
                     }
-                    ax[13] += syh * w; ax[14] += syh * wu; ax[15] += syh * wv; ax[16] += syh * wq; ax[17] += syb * w;
-                    ay[13] += sxh * w; ay[14] += sxh * wu; ay[15] += sxh * wv; ay[16] += sxh * wq; ay[17] += sxb * w;
-                    const T txh = u * (u * sxh + v * syh), tyh = v * (v * syh + u * sxh);
-                    ax[18] += txh * w; ax[19] += txh * wu; ax[20] += txh * wv; ax[21] += txh * wq;
-                    ay[18] += tyh * w; ay[19] += tyh * wu; ay[20] += tyh * wv; ay[21] += tyh * wq;
-                    ax[22] += u * (u * sxb + v * syb) * w;
-                    ay[22] += v * (v * syb + u * sxb) * w;
+#pragma unroll
+                    for (int q = 3; q < 10; ++q) {
+                        xs[q - 3] += dx.x * m[q];
+                        ys[q - 3] += dy.x * m[q];
+                        csm[q - 3] += f0.x * m[q];
+                    }
+                    xp[3] = pfma(syv, bc(w), xp[3]); xs[7] += syh * wu; xs[8] += syh * wv; xs[9] += syh * wq;
+                    yp[3] = pfma(sxv, bc(w), yp[3]); ys[7] += sxh * wu; ys[8] += sxh * wv; ys[9] += sxh * wq;
+                    xp[4] = pfma(tx, bc(w), xp[4]); xs[10] += tx.x * wu; xs[11] += tx.x * wv; xs[12] += tx.x * wq;
+                    yp[4] = pfma(ty, bc(w), yp[4]); ys[10] += ty.x * wu; ys[11] += ty.x * wv; ys[12] += ty.x * wq;
                 }
             }
         }
@@ -357,6 +412,12 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
     }
     if (!valid) return;
     if (cur >= 0) flush();
+    if constexpr (!SEP) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) { ac[q] = cp2[q].x; ac[10 + q] = cp2[q].y; }
+#pragma unroll
+        for (int q = 0; q < 7; ++q) ac[3 + q] = csm[q];
+    }
     const T cm = lane_totals<NCM>(ac, lane);
     __syncwarp();
     const int c = j * nx + i;
@@ -437,21 +498,23 @@ struct alignas(16) K4Copy {
     int kind;
 };
 
-// Shared-memory layout of k4_cells (byte offsets, pairs for distributions, each block 16-byte aligned):
-//   own   [nt][NCT][32] pairs      the tile's own cells on every level (spectral source, h^k of the update)
-//   rect  [2][NR][32] pairs        per level: the tile with its halo, (TX+3) x (TY+3) cells, two cells on the
-//                                  upwind side of each axis and one on the downwind side (ring of 2 levels)
-//   fp    [2][NFT][NP] T           per level: parameters of the tile's faces (ring of 2 levels)
-//   cp    [2][NCT][NCP] T          per level: update coefficients of the tile's cells (ring of 2 levels)
-//   flux  [2][NFT][32] pairs       per level: micro fluxes of the tile's faces (double buffered)
-template <typename T, int TX, int TY>
+// Shared-memory layout of k4_cells (byte offsets, pairs for distributions, each block 16-byte aligned).  A CTA
+// owns VPL velocity blocks of one sign class (h = 0..VPL-1 below), and each lane one velocity of every block:
+//   own   [nt][VPL][NCT][32] pairs   the tile's own cells on every level: h^k as loaded; in the explicit form
+//                                    replaced once by the spectral source of every level
+//   rect  [2][VPL][NR][32] pairs     per level: the tile with its halo, (TX+3) x (TY+3) cells, two cells on
+//                                    the upwind side of each axis and one on the downwind side (ring of 2)
+//   fp    [2][NFT][NP] T             per level: parameters of the tile's faces (ring of 2 levels)
+//   cp    [2][NCT][NCP] T            per level: update coefficients of the tile's cells (ring of 2 levels)
+//   flux  [2][VPL][NFT][32] pairs    per level: micro fluxes of the tile's faces (double buffered)
+template <typename T, int TX, int TY, int VPL>
 struct K4Layout {
     using V = P2<T>;
     static constexpr int PX = TX + 3, PY = TY + 3, NR = PX * PY, NCT = TX * TY;
     static constexpr int NFX = TY * (TX + 1), NFY = (TY + 1) * TX, NFT = NFX + NFY;
-    static constexpr size_t RECT = (size_t)NR * VB;                     // pairs per ring slot
-    static constexpr size_t FP = (size_t)NFT * NP, CP = (size_t)NCT * NCP, FLUX = (size_t)NFT * VB;
-    __host__ __device__ static constexpr size_t own_bytes(int nt) { return (size_t)nt * NCT * VB * sizeof(V); }
+    static constexpr size_t RECT = (size_t)VPL * NR * VB;               // pairs per ring slot
+    static constexpr size_t FP = (size_t)NFT * NP, CP = (size_t)NCT * NCP, FLUX = (size_t)VPL * NFT * VB;
+    __host__ __device__ static constexpr size_t own_bytes(int nt) { return (size_t)nt * VPL * NCT * VB * sizeof(V); }
     __host__ __device__ static constexpr size_t rect_off(int nt) { return own_bytes(nt); }
     __host__ __device__ static constexpr size_t fp_off(int nt) { return rect_off(nt) + 2 * RECT * sizeof(V); }
     __host__ __device__ static constexpr size_t cp_off(int nt) { return fp_off(nt) + 2 * FP * sizeof(T); }
@@ -459,23 +522,28 @@ struct K4Layout {
     __host__ __device__ static constexpr size_t bytes(int nt) { return flux_off(nt) + 2 * FLUX * sizeof(V); }
 };
 
-// A CTA: a TX x TY tile of cells, one velocity block, all levels.  Per level, the first pass reconstructs
-// every tile cell and the upwind halo cells and evaluates the flux through each one's downwind face (every
-// face of the tile exactly once); the second pass applies Eq. fv_h to the tile cells.  The second pass of
-// level n runs together with the first pass of level n + 1 (fluxes double buffered), so one barrier separates
-// the levels.  With IMP and a case that asks for it, the spectral source is taken at the new iterate: pass 2
-// leaves each level's right-hand side in the own-cell store and a last pass applies the per-cell inverse
-// across levels.  Batch k of bulk copies (the halo rectangle and face parameters of level k, the cell
-// coefficients of level k - 1; batch 0 also every level of the tile's own cells) completes on mbarrier k & 1
-// and is issued one level ahead of its use.
-template <typename T, int TX, int TY, int NW, bool IMP>
+// A CTA: a TX x TY tile of cells, VPL velocity blocks of one sign class, all levels.  Per level, the first pass
+// reconstructs every tile cell and the upwind halo cells and evaluates the flux through each one's downwind
+// face (every face of the tile exactly once); the second pass applies Eq. fv_h to the tile cells.  Each item
+// (a cell of a pass) forms its indices, addresses and face or cell parameters once and serves the lane's
+// velocity in each of the VPL blocks.  The second pass of level n runs in the same barrier interval as the
+// first pass of level n + 1 (fluxes double buffered), so one barrier separates the levels.  In the explicit
+// form the spectral source of every level is formed once per CTA, in place in the own-cell store, and each
+// warp keeps h^k of its pass-2 cells from pass 1.  With IMP and a case that asks for it, the spectral source is
+// taken at the new iterate instead: pass 2 leaves each level's right-hand side in the own-cell store and a last
+// pass applies the per-cell inverse across levels.  Batch k of bulk copies (the halo rectangle and face
+// parameters of level k, the cell coefficients of level k - 1; batch 0 also every level of the tile's own
+// cells) completes on mbarrier k & 1 and is issued one level ahead of its use.
+template <typename T, int TX, int TY, int NW, bool IMP, int VPL>
 __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
 {
-    using L = K4Layout<T, TX, TY>;
+    using L = K4Layout<T, TX, TY, VPL>;
     using V = P2<T>;
-    constexpr int PX = L::PX, PY = L::PY, NCT = L::NCT, NFX = L::NFX;
+    constexpr int PX = L::PX, PY = L::PY, NR = L::NR, NCT = L::NCT, NFX = L::NFX, NFT = L::NFT;
     constexpr int NIT = NCT + TY + TX, NPASS = (NIT + NW - 1) / NW;
+    constexpr int NP2 = (NCT + NW - 1) / NW;                  // tile cells per warp in pass 2
     constexpr int SROWS = 4;                                  // tile rows per strip of the CTA order
+    constexpr int LVO = VPL * NCT * VB;                       // level stride of the own-cell store (pairs)
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ uint64_t bars[2];
     __shared__ T gxr[PX], gxh[PX], gyr[PY], gyh[PY];
@@ -485,11 +553,11 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
     // another CTA may set the error word while this one starts: decide for the whole CTA at once
     if (__syncthreads_or(*(volatile int*)cd.err != 0)) return;
     const bool expire = *(volatile const int*)cd.expire != 0;
-    const int nvb = cd.nvb, nx = cd.nx, ny = cd.ny;
-    // CTA order: velocity block fastest (the CTAs of one tile share its parameters in L2), then tiles in
+    const int nvg = cd.nvb / VPL, nx = cd.nx, ny = cd.ny;
+    // CTA order: velocity group fastest (the CTAs of one tile share its parameters in L2), then tiles in
     // strips of SROWS tile rows, column by column (neighbour tiles, whose halos overlap, run close in time)
     const int lb = blockIdx.x - B.off[cs];
-    const int vb = lb % nvb, tile = lb / nvb;
+    const int vb = (lb % nvg) * VPL, tile = lb / nvg;         // vb: the CTA's first velocity block
     const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY;
     const int strip = tile / (ntx * SROWS), rows = min(SROWS, nty - strip * SROWS);
     const int rem = tile - strip * ntx * SROWS;
@@ -509,6 +577,7 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
     mbar_setup(bars, 2);
     const int p = cd.st->parity;
     const V* gf = cd.f[p];
+    const size_t bstride = (size_t)nt * nc * VB;              // pairs between consecutive velocity blocks
     // bulk copies of the rectangle rows (clipped to the domain)
     const int c0 = max(i0 + xlo, 0), c1 = min(i0 + xlo + PX, nx);
     const int nfr = iend - i0;                                // valid cells per tile row
@@ -518,59 +587,49 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
         const int jj = j0 + ylo + r;
         rrows += (jj >= 0 && jj < ny) ? 1 : 0;
     }
-    const uint32_t rect_b = (uint32_t)rrows * row_b;
+    const uint32_t rect_b = (uint32_t)(VPL * rrows) * row_b;
     const uint32_t fp_b = (uint32_t)(((jend - j0) * (nfr + 1) + (jend - j0 + 1) * nfr) * NP * sizeof(T));
     const uint32_t cp_b = (uint32_t)((jend - j0) * nfr * NCP * sizeof(T));
-    // batch k: rectangle and face parameters of level k (k < nt), cell coefficients of level k - 1 (k >= 1)
-    auto issue = [&](int k) {
-        const bool lvl = k < nt, cel = k >= 1;
-        uint32_t bytes = (lvl ? rect_b + fp_b : 0u) + (cel ? cp_b : 0u);
-        if (k == 0) bytes += (uint32_t)(nt * (jend - j0) * nfr * VB * sizeof(V));
-        uint64_t* bar = &bars[k & 1];
-        if (lane == 0) mbar_arrive_expect(bar, bytes);
-        __syncwarp();
-        const int nrect = lvl ? PY : 0, nfpr = lvl ? 2 * TY + 1 : 0, ncpr = cel ? TY : 0;
-        const int nown = k == 0 ? nt * TY : 0;
-        for (int q = lane; q < nrect + nfpr + ncpr + nown; q += 32) {
-            if (q < nrect) {
-                const int r = q, jj = j0 + ylo + r;
-                if (jj < 0 || jj >= ny) continue;
-                const size_t src = ((size_t)vb * nt + k) * nc * VB + ((size_t)jj * nx + c0) * VB;
-                bulk_g2s(rect + (size_t)(k & 1) * L::RECT + (size_t)(r * PX + c0 - (i0 + xlo)) * VB, gf + src, row_b,
-                         bar);
-            } else if (q < nrect + nfpr) {
-                const int r = q - nrect;
-                if (r < TY) {                                 // x-faces of tile row r
-                    const int jj = j0 + r;
+    // batch 0 (warp 0): rectangle and face parameters of level 0, every level of the own cells
+    {
+        constexpr int NRECT = VPL * PY, NFPR = 2 * TY + 1;
+        const int nown = nt * VPL * TY;
+        if (warp == 0) {
+            if (lane == 0)
+                mbar_arrive_expect(&bars[0], rect_b + fp_b + (uint32_t)(nt * VPL * (jend - j0) * nfr * VB * sizeof(V)));
+            __syncwarp();
+            for (int q = lane; q < NRECT + NFPR + nown; q += 32) {
+                if (q < NRECT) {
+                    const int h = q / PY, r = q % PY, jj = j0 + ylo + r;
+                    if (jj < 0 || jj >= ny) continue;
+                    bulk_g2s(rect + (size_t)(h * NR + r * PX + c0 - (i0 + xlo)) * VB,
+                             gf + (vb + h) * bstride + ((size_t)jj * nx + c0) * VB, row_b, &bars[0]);
+                } else if (q < NRECT + NFPR) {
+                    const int r = q - NRECT;
+                    if (r < TY) {                             // x-faces of tile row r
+                        const int jj = j0 + r;
+                        if (jj >= ny) continue;
+                        bulk_g2s(fps + (size_t)r * (TX + 1) * NP, cd.fpar + ((size_t)jj * (nx + 1) + i0) * NP,
+                                 (uint32_t)((nfr + 1) * NP * sizeof(T)), &bars[0]);
+                    } else {                                  // y-faces of face row r - TY
+                        const int fr = r - TY, jj = j0 + fr;
+                        if (jj > jend) continue;
+                        bulk_g2s(fps + (size_t)(NFX + fr * TX) * NP, cd.fpar + ((size_t)nfx + (size_t)jj * nx + i0) * NP,
+                                 (uint32_t)(nfr * NP * sizeof(T)), &bars[0]);
+                    }
+                } else {
+                    const int o = q - NRECT - NFPR;           // own cells: row, block, level
+                    const int r = o % TY, h = (o / TY) % VPL, n = o / (TY * VPL), jj = j0 + r;
                     if (jj >= ny) continue;
-                    bulk_g2s(fps + (size_t)(k & 1) * L::FP + (size_t)r * (TX + 1) * NP,
-                             cd.fpar + ((size_t)k * nf + jj * (nx + 1) + i0) * NP,
-                             (uint32_t)((nfr + 1) * NP * sizeof(T)), bar);
-                } else {                                      // y-faces of face row r - TY
-                    const int fr = r - TY, jj = j0 + fr;
-                    if (jj > jend) continue;
-                    bulk_g2s(fps + (size_t)(k & 1) * L::FP + (size_t)(NFX + fr * TX) * NP,
-                             cd.fpar + ((size_t)k * nf + nfx + jj * nx + i0) * NP, (uint32_t)(nfr * NP * sizeof(T)),
-                             bar);
+                    bulk_g2s(own + ((size_t)(n * VPL + h) * NCT + r * TX) * VB,
+                             gf + (vb + h) * bstride + (size_t)n * nc * VB + ((size_t)jj * nx + i0) * VB,
+                             (uint32_t)(nfr * VB * sizeof(V)), &bars[0]);
                 }
-            } else if (q < nrect + nfpr + ncpr) {
-                const int r = q - nrect - nfpr, jj = j0 + r;  // cells of tile row r, level k - 1
-                if (jj >= ny) continue;
-                bulk_g2s(cps + (size_t)((k - 1) & 1) * L::CP + (size_t)r * TX * NCP,
-                         cd.cpar + ((size_t)(k - 1) * nc + jj * nx + i0) * NCP, (uint32_t)(nfr * NCP * sizeof(T)), bar);
-            } else {
-                const int o = q - nrect - nfpr - ncpr;        // own cells: row, level
-                const int r = o % TY, n = o / TY, jj = j0 + r;
-                if (jj >= ny) continue;
-                bulk_g2s(own + ((size_t)n * NCT + r * TX) * VB,
-                         gf + ((size_t)vb * nt + n) * nc * VB + ((size_t)jj * nx + i0) * VB,
-                         (uint32_t)(nfr * VB * sizeof(V)), bar);
             }
         }
-    };
-    if (warp == 0) issue(0);
+    }
     // the copies of batches 1..nt, formed once: at each level warp 0 then only offsets them
-    constexpr int NQ = PY + 2 * TY + 1 + TY;
+    constexpr int NQ = VPL * PY + 2 * TY + 1 + TY;
     static_assert(NQ <= 32, "one lane of warp 0 per copy of a batch");
     __shared__ K4Copy cpy[32];
     if (warp == 0 && lane < NQ) {
@@ -581,18 +640,17 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
         c.dst = 0;
         c.dslot = 0;
         c.kind = 0;
-        if (lane < PY) {
-            const int r = lane, jj = j0 + ylo + r;
-            c.kind = 0;
+        if (lane < VPL * PY) {
+            const int h = lane / PY, r = lane % PY, jj = j0 + ylo + r;
             if (jj >= 0 && jj < ny) {
-                c.src = reinterpret_cast<const char*>(gf + (size_t)vb * nt * nc * VB + ((size_t)jj * nx + c0) * VB);
+                c.src = reinterpret_cast<const char*>(gf + (vb + h) * bstride + ((size_t)jj * nx + c0) * VB);
                 c.sstride = (long long)nc * VB * sizeof(V);
-                c.dst = smem_u32(rect + (size_t)(r * PX + c0 - (i0 + xlo)) * VB);
+                c.dst = smem_u32(rect + (size_t)(h * NR + r * PX + c0 - (i0 + xlo)) * VB);
                 c.dslot = (uint32_t)(L::RECT * sizeof(V));
                 c.bytes = row_b;
             }
-        } else if (lane < PY + 2 * TY + 1) {
-            const int r = lane - PY;
+        } else if (lane < VPL * PY + 2 * TY + 1) {
+            const int r = lane - VPL * PY;
             c.kind = 1;
             c.sstride = (long long)nf * NP * sizeof(T);
             c.dslot = (uint32_t)(L::FP * sizeof(T));
@@ -612,7 +670,7 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
                 }
             }
         } else {
-            const int r = lane - PY - 2 * TY - 1, jj = j0 + r;  // cells of tile row r
+            const int r = lane - VPL * PY - 2 * TY - 1, jj = j0 + r;   // cells of tile row r
             c.kind = 2;
             if (jj < ny) {
                 c.src = reinterpret_cast<const char*>(cd.cpar + ((size_t)jj * nx + i0) * NCP);
@@ -649,14 +707,22 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
         gyr[k] = (jj >= 0 && jj < ny - 1) ? T(cd.rdy[jj]) : T(0);
         gyh[k] = (jj >= 0 && jj < ny) ? T(cd.hy[jj]) : T(0);
     }
-    const int av = vb * VB + lane;
-    const T u = __ldg(cd.tu + av), v = __ldg(cd.tv + av), href = __ldg(cd.thref + av);
-    const T r2 = u * u + v * v;
-    const V ub = bc(u), vbb = bc(v);
-    const int iu = __ldg(cd.viu + av), ivn = cd.nu + __ldg(cd.viv + av);
-    V etb[8];
+    // the lane's velocity in each of the CTA's blocks
+    T u[VPL], v[VPL], href[VPL], r2[VPL];
+    int iu[VPL], ivn[VPL];
 #pragma unroll
-    for (int d = 0; d < 8; ++d) etb[d] = bc(cd.et[d]);
+    for (int h = 0; h < VPL; ++h) {
+        const int av = (vb + h) * VB + lane;
+        u[h] = __ldg(cd.tu + av);
+        v[h] = __ldg(cd.tv + av);
+        href[h] = __ldg(cd.thref + av);
+        r2[h] = u[h] * u[h] + v[h] * v[h];
+        iu[h] = __ldg(cd.viu + av);
+        ivn[h] = cd.nu + __ldg(cd.viv + av);
+    }
+    V etb[IMP ? 8 : 1];                                       // implicit-capable kernels: e_d as pairs
+#pragma unroll
+    for (int d = 0; d < (IMP ? 8 : 1); ++d) etb[d] = bc(cd.et[d]);
     const T* __restrict__ ftab = cd.ftab;
     const T* __restrict__ wtab = cd.wtab;
     const T* __restrict__ ctab = cd.ctab;
@@ -671,14 +737,234 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
     // of each exists
     const bool interior = i0 >= 2 && j0 >= 2 && i0 + TX <= nx - 2 && j0 + TY <= ny - 2;
     constexpr bool PAIRED = NCT == 2 * NW;                    // each warp owns two tile cells in pass 1
+    V f0k[NP2][VPL];                                          // h^k of the warp's pass-2 cells (explicit form)
+#pragma unroll
+    for (int r = 0; r < NP2; ++r)
+#pragma unroll
+        for (int h = 0; h < VPL; ++h) f0k[r][h] = bc(T(0));
 
+    __syncthreads();                                          // the spacing tables above, for every warp
     for (int s = 0; s <= nt; ++s) {
         if (warp == 0 && s < nt) issue_next(s + 1);
         // the test hook reports the first wait as expired only after it has completed
         const int fail = !mbar_wait(&bars[s & 1], (uint32_t)((s >> 1) & 1), err) || expire;
+        if (!fail) {
+            if (!IMP && s == 0) {
+                // the spectral source of every level of the warp's own cells, once, in place of h^k
+#pragma unroll
+                for (int r = 0; r < NP2; ++r) {
+                    const int ct = warp + r * NW;
+                    if (ct >= NCT) break;
+                    if (i0 + ct % TX >= nx || j0 + ct / TX >= ny) continue;
+#pragma unroll
+                    for (int h = 0; h < VPL; ++h) {
+                        V* fc = own + (size_t)(h * NCT + ct) * VB + lane;
+                        switch (nh) {
+                            case 0: spectral_all<0>(fc, LVO, cd.et); break;
+                            case 1: spectral_all<1>(fc, LVO, cd.et); break;
+                            case 2: spectral_all<2>(fc, LVO, cd.et); break;
+                            case 3: spectral_all<3>(fc, LVO, cd.et); break;
+                            case 4: spectral_all<4>(fc, LVO, cd.et); break;
+                            case 5: spectral_all<5>(fc, LVO, cd.et); break;
+                            case 6: spectral_all<6>(fc, LVO, cd.et); break;
+                            default: spectral_all<7>(fc, LVO, cd.et); break;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            if (s > 0) {
+                // ---- pass 2, level s - 1 (ahead of pass 1 of level s, which refills f0k): Eq. fv_h with the
+                // spectral source (delta form)
+                const int n = s - 1;
+                const V* F = fbuf + (size_t)(n & 1) * L::FLUX + lane;
+                V* on = cd.f[p ^ 1] + vb * bstride + (size_t)n * nc * VB + lane;
+                const T* cpn = cps + (size_t)(n & 1) * L::CP;
+                const T* ctn = ctab + n * 2 * nuv;
+#pragma unroll
+                for (int r = 0; r < NP2; ++r) {
+                    const int ct = warp + r * NW;
+                    if (ct >= NCT) break;
+                    const int ti = ct % TX, tj = ct / TX;
+                    const int i = i0 + ti, j = j0 + tj;
+                    if (i >= nx || j >= ny) continue;
+                    const int c = j * nx + i;
+                    const T* tb = ctn + c * nt * 2 * nuv;
+                    const int fL = tj * (TX + 1) + ti, fB = NFX + tj * TX + ti;
+                    const T* cp = cpn + ct * NCP;
+                    const V* k = reinterpret_cast<const V*>(cp + C_K);   // kself, -kE, kp1, kp0, -kdx, -kdy
+#pragma unroll
+                    for (int h = 0; h < VPL; ++h) {
+                        const T ex0 = __ldg(tb + iu[h]), ey0 = __ldg(tb + ivn[h]);
+                        const T ex1 = __ldg(tb + nuv + iu[h]), ey1 = __ldg(tb + nuv + ivn[h]);
+                        const V* Fh = F + (size_t)h * NFT * VB;
+                        const V dX = psub(Fh[(fL + 1) * VB], Fh[fL * VB]);
+                        const V dY = psub(Fh[(fB + TX) * VB], Fh[fB * VB]);
+                        V* fc = own + (size_t)(h * NCT + ct) * VB + lane;   // level m at fc[m * LVO]
+                        V e, f0;
+                        if constexpr (!IMP) {
+                            e = fc[n * LVO];                  // precomputed
+                            f0 = f0k[r][h];
+                        } else {
+                            switch (implicit ? 0 : nh) {
+                                case 0: e = etb[0]; break;
+                                case 1: e = spectral2<1>(fc, n, nt, LVO, etb); break;
+                                case 2: e = spectral2<2>(fc, n, nt, LVO, etb); break;
+                                case 3: e = spectral2<3>(fc, n, nt, LVO, etb); break;
+                                case 4: e = spectral2<4>(fc, n, nt, LVO, etb); break;
+                                case 5: e = spectral2<5>(fc, n, nt, LVO, etb); break;
+                                case 6: e = spectral2<6>(fc, n, nt, LVO, etb); break;
+                                default: e = spectral2<7>(fc, n, nt, LVO, etb); break;
+                            }
+                            f0 = fc[n * LVO];
+                        }
+                        // equilibria of W^{k+1} (slot 1) and W^k (slot 0), delta form
+                        const V q1 = eq2(cp + C_EQ1, ex1, ey1, href[h], u[h], v[h], r2[h], shakhov);
+                        const V q0 = eq2(cp + C_EQ0, ex0, ey0, href[h], u[h], v[h], r2[h], shakhov);
+                        V x = pmul(k[0], f0);
+                        x = pfma(k[4], dX, x);
+                        x = pfma(k[5], dY, x);
+                        x = pfma(k[1], e, x);
+                        x = pfma(k[2], q1, x);
+                        x = pfma(k[3], q0, x);
+                        if (implicit) fc[n * LVO] = x;       // right-hand side of level n; h^k no longer needed
+                        else on[h * bstride + (size_t)c * VB] = x;
+                    }
+                }
+            }
+            if (s < nt) {
+                // ---- pass 1, level s: reconstruction and downwind-face fluxes
+                const int n = s;
+                V* F = fbuf + (size_t)(n & 1) * L::FLUX + lane;
+                const V* rh = rect + (size_t)(n & 1) * L::RECT + lane;
+                const T* fpn = fps + (size_t)(n & 1) * L::FP;
+                const T* ftn = ftab + n * nuv;
+                int rfirst = 0;
+                if (PAIRED && interior) {
+                    // both tile cells of the warp, every block, as one straight-line block, stores last, so that
+                    // the independent chains interleave
+                    V fl[2][VPL][2];
+                    int sl[2][2];
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const int it = warp + q * NW, ti = it % TX, tj = it / TX;
+                        const int i = i0 + ti, j = j0 + tj;
+                        const int kx = ti - xlo, ky = tj - ylo;
+                        const int fix = xneg ? i : i + 1, fjy = yneg ? j : j + 1;
+                        sl[q][0] = tj * (TX + 1) + fix - i0;
+                        sl[q][1] = NFX + (fjy - j0) * TX + ti;
+                        const T* tbx = ftn + (j * (nx + 1) + fix) * NTf;
+                        const T* tby = ftn + (nfx + fjy * nx + i) * NTf;
+                        const T wxm = gxr[kx - 1], wxp = gxr[kx], wym = gyr[ky - 1], wyp = gyr[ky];
+                        const V hx = bc(xneg ? -gxh[kx] : gxh[kx]), hy = bc(yneg ? -gyh[ky] : gyh[ky]);
+#pragma unroll
+                        for (int h = 0; h < VPL; ++h) {
+                            const T exx = __ldg(tbx + iu[h]), eyx = __ldg(tbx + ivn[h]);
+                            const T exy = __ldg(tby + iu[h]), eyy = __ldg(tby + ivn[h]);
+                            const V* ph = rh + (size_t)(h * NR + ky * PX + kx) * VB;
+                            const V f0 = ph[0];
+                            f0k[q][h] = f0;
+                            const V sxv = slope2i(ph[-VB], f0, ph[VB], wxm, wxp);
+                            const V syv = slope2i(ph[-PX * VB], f0, ph[PX * VB], wym, wyp);
+                            const V dx0 = pfma(sxv, hx, f0);
+                            const V dy0 = pfma(syv, hy, f0);
+                            const V ub = bc(u[h]), vbb = bc(v[h]);
+                            fl[q][h][0] = flux2(fpn + sl[q][0] * NP, qoff, loff, exx, eyx, href[h], u[h], v[h], ub, vbb,
+                                                dx0, sxv, syv);
+                            fl[q][h][1] = flux2(fpn + sl[q][1] * NP, qoffy, loffy, exy, eyy, href[h], u[h], v[h], vbb,
+                                                ub, dy0, syv, sxv);
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < 2; ++q)
+#pragma unroll
+                        for (int h = 0; h < VPL; ++h) {
+                            F[(h * NFT + sl[q][0]) * VB] = fl[q][h][0];
+                            F[(h * NFT + sl[q][1]) * VB] = fl[q][h][1];
+                        }
+                    rfirst = 2;
+                }
+#pragma unroll
+                for (int r = 0; r < NPASS; ++r) {
+                    if (r < rfirst) continue;
+                    const int it = warp + r * NW;
+                    if (it >= NIT) break;
+                    int ti, tj;
+                    bool dox = true, doy = true;
+                    if ((r + 1) * NW <= NCT || it < NCT) {
+                        ti = it % TX; tj = it / TX;
+                        if (i0 + ti >= nx || j0 + tj >= ny) continue;
+                    } else if (it < NCT + TY) {
+                        tj = it - NCT; ti = xneg ? iend - i0 : -1; doy = false;
+                        if (j0 + tj >= ny) continue;
+                    } else {
+                        ti = it - NCT - TY; tj = yneg ? jend - j0 : -1; dox = false;
+                        if (i0 + ti >= nx) continue;
+                    }
+                    const int i = i0 + ti, j = j0 + tj;
+                    if (!interior && (i < 0 || i >= nx || j < 0 || j >= ny)) {
+                        // upwind face of the tile on a wall: the re-emitted distribution
+                        int slot;
+                        const T* wt;
+                        if (dox) {
+                            const int fi = i < 0 ? 0 : nx;
+                            slot = tj * (TX + 1) + fi - i0;
+                            wt = wtab + ((i < 0 ? 3 : 1) * cd.nslot + wall_slot(cd, n)) * nuv;
+                        } else {
+                            const int fj = j < 0 ? 0 : ny;
+                            slot = NFX + (fj - j0) * TX + ti;
+                            wt = wtab + ((j < 0 ? 0 : 2) * cd.nslot + wall_slot(cd, n)) * nuv;
+                        }
+#pragma unroll
+                        for (int h = 0; h < VPL; ++h)
+                            F[(h * NFT + slot) * VB] = flux_wall2(fpn + slot * NP, wt, iu[h], ivn[h], href[h],
+                                                                  bc(dox ? u[h] : v[h]));
+                        continue;
+                    }
+                    const int kx = ti - xlo, ky = tj - ylo;
+                    const int fix = xneg ? i : i + 1, fjy = yneg ? j : j + 1;
+                    const int slx = tj * (TX + 1) + fix - i0, sly = NFX + (fjy - j0) * TX + ti;
+                    const T* tbx = ftn + (j * (nx + 1) + fix) * NTf;
+                    const T* tby = ftn + (nfx + fjy * nx + i) * NTf;
+                    const T wxm = gxr[kx - 1], wxp = gxr[kx], wym = gyr[ky - 1], wyp = gyr[ky];
+#pragma unroll
+                    for (int h = 0; h < VPL; ++h) {
+                        // expm1 factors of the interface Maxwellians first: their latency overlaps the
+                        // reconstruction
+                        T exx = T(0), eyx = T(0), exy = T(0), eyy = T(0);
+                        if (dox) { exx = __ldg(tbx + iu[h]); eyx = __ldg(tbx + ivn[h]); }
+                        if (doy) { exy = __ldg(tby + iu[h]); eyy = __ldg(tby + ivn[h]); }
+                        const V* ph = rh + (size_t)(h * NR + ky * PX + kx) * VB;
+                        const V f0 = ph[0];
+                        if (r < NP2 && it < NCT) f0k[r][h] = f0;
+                        V sxv, syv;
+                        if (interior) {
+                            sxv = slope2i(ph[-VB], f0, ph[VB], wxm, wxp);
+                            syv = slope2i(ph[-PX * VB], f0, ph[PX * VB], wym, wyp);
+                        } else {
+                            sxv = slope2(ph[-VB], f0, ph[VB], wxm, wxp, i > 0, i < nx - 1, nx > 1);
+                            syv = slope2(ph[-PX * VB], f0, ph[PX * VB], wym, wyp, j > 0, j < ny - 1, ny > 1);
+                        }
+                        const V ub = bc(u[h]), vbb = bc(v[h]);
+                        if (dox) {
+                            const V d0 = pfma(sxv, bc(xneg ? -gxh[kx] : gxh[kx]), f0);
+                            F[(h * NFT + slx) * VB] = flux2(fpn + slx * NP, qoff, loff, exx, eyx, href[h], u[h], v[h],
+                                                            ub, vbb, d0, sxv, syv);
+                        }
+                        if (doy) {
+                            const V d0 = pfma(syv, bc(yneg ? -gyh[ky] : gyh[ky]), f0);
+                            F[(h * NFT + sly) * VB] = flux2(fpn + sly * NP, qoffy, loffy, exy, eyy, href[h], u[h],
+                                                            v[h], vbb, ub, d0, syv, sxv);
+                        }
+                    }
+                }
+            }
+        }
+        // one barrier per level: it publishes this level's fluxes, frees the ring slots read here, and makes
+        // the CTA agree on a failed wait
         if (__syncthreads_or(fail)) {
-            // every thread agrees; warp 0, which issued them, waits (bounded) for batches s and s + 1, so that
-            // no bulk copy still lands in shared memory after the CTA exits
+            // warp 0, which issued them, waits (bounded) for batches s and s + 1, so that no bulk copy still
+            // lands in shared memory after the CTA exits
             if (threadIdx.x == 0 && expire) atomicExch(err, 1);
             if (warp == 0) {
                 mbar_drain(&bars[s & 1], (uint32_t)((s >> 1) & 1));
@@ -686,196 +972,41 @@ __global__ void __launch_bounds__(NW * 32) k4_cells(Batch<T> B)
             }
             return;
         }
-        if (s < nt) {
-            // ---- pass 1, level s: reconstruction and downwind-face fluxes
-            const int n = s;
-            V* F = fbuf + (size_t)(n & 1) * L::FLUX + lane;
-            const V* rh = rect + (size_t)(n & 1) * L::RECT + lane;
-            const T* fpn = fps + (size_t)(n & 1) * L::FP;
-            const T* ftn = ftab + n * nuv;
-            int rfirst = 0;
-            if (PAIRED && interior) {
-                // both tile cells of the warp as one straight-line block, stores last, so that the two
-                // independent chains interleave
-                V fl[2][2];
-                int sl[2][2];
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int it = warp + q * NW, ti = it % TX, tj = it / TX;
-                    const int i = i0 + ti, j = j0 + tj;
-                    const int kx = ti - xlo, ky = tj - ylo;
-                    const int fix = xneg ? i : i + 1, fjy = yneg ? j : j + 1;
-                    sl[q][0] = tj * (TX + 1) + fix - i0;
-                    sl[q][1] = NFX + (fjy - j0) * TX + ti;
-                    const T* tbx = ftn + (j * (nx + 1) + fix) * NTf;
-                    const T* tby = ftn + (nfx + fjy * nx + i) * NTf;
-                    const T exx = __ldg(tbx + iu), eyx = __ldg(tbx + ivn);
-                    const T exy = __ldg(tby + iu), eyy = __ldg(tby + ivn);
-                    const V* ph = rh + (ky * PX + kx) * VB;
-                    const V f0 = ph[0];
-                    const V sxv = slope2i(ph[-VB], f0, ph[VB], gxr[kx - 1], gxr[kx]);
-                    const V syv = slope2i(ph[-PX * VB], f0, ph[PX * VB], gyr[ky - 1], gyr[ky]);
-                    const V dx0 = pfma(sxv, bc(xneg ? -gxh[kx] : gxh[kx]), f0);
-                    const V dy0 = pfma(syv, bc(yneg ? -gyh[ky] : gyh[ky]), f0);
-                    fl[q][0] = flux2(fpn + sl[q][0] * NP, qoff, loff, exx, eyx, href, u, v, ub, vbb, dx0, sxv, syv);
-                    fl[q][1] = flux2(fpn + sl[q][1] * NP, qoffy, loffy, exy, eyy, href, u, v, vbb, ub, dy0, syv, sxv);
-                }
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    F[sl[q][0] * VB] = fl[q][0];
-                    F[sl[q][1] * VB] = fl[q][1];
-                }
-                rfirst = 2;
-            }
-#pragma unroll
-            for (int r = 0; r < NPASS; ++r) {
-                if (r < rfirst) continue;
-                const int it = warp + r * NW;
-                if (it >= NIT) break;
-                int ti, tj;
-                bool dox = true, doy = true;
-                if ((r + 1) * NW <= NCT || it < NCT) {
-                    ti = it % TX; tj = it / TX;
-                    if (i0 + ti >= nx || j0 + tj >= ny) continue;
-                } else if (it < NCT + TY) {
-                    tj = it - NCT; ti = xneg ? iend - i0 : -1; doy = false;
-                    if (j0 + tj >= ny) continue;
-                } else {
-                    ti = it - NCT - TY; tj = yneg ? jend - j0 : -1; dox = false;
-                    if (i0 + ti >= nx) continue;
-                }
-                const int i = i0 + ti, j = j0 + tj;
-                if (!interior && (i < 0 || i >= nx || j < 0 || j >= ny)) {
-                    // upwind face of the tile on a wall: the re-emitted distribution
-                    V Fw;
-                    int slot;
-                    if (dox) {
-                        const int fi = i < 0 ? 0 : nx;
-                        slot = tj * (TX + 1) + fi - i0;
-                        Fw = flux_wall2(fpn + slot * NP, wtab + ((i < 0 ? 3 : 1) * cd.nslot + wall_slot(cd, n)) * nuv,
-                                        iu, ivn, href, ub);
-                    } else {
-                        const int fj = j < 0 ? 0 : ny;
-                        slot = NFX + (fj - j0) * TX + ti;
-                        Fw = flux_wall2(fpn + slot * NP, wtab + ((j < 0 ? 0 : 2) * cd.nslot + wall_slot(cd, n)) * nuv,
-                                        iu, ivn, href, vbb);
-                    }
-                    F[slot * VB] = Fw;
-                    continue;
-                }
-                const int kx = ti - xlo, ky = tj - ylo;
-                const int fix = xneg ? i : i + 1, fjy = yneg ? j : j + 1;
-                const int slx = tj * (TX + 1) + fix - i0, sly = NFX + (fjy - j0) * TX + ti;
-                // expm1 factors of the interface Maxwellians first: their latency overlaps the reconstruction
-                const T* tbx = ftn + (j * (nx + 1) + fix) * NTf;
-                const T* tby = ftn + (nfx + fjy * nx + i) * NTf;
-                T exx = T(0), eyx = T(0), exy = T(0), eyy = T(0);
-                if (dox) { exx = __ldg(tbx + iu); eyx = __ldg(tbx + ivn); }
-                if (doy) { exy = __ldg(tby + iu); eyy = __ldg(tby + ivn); }
-                const V* ph = rh + (ky * PX + kx) * VB;
-                const V f0 = ph[0];
-                const T wxm = gxr[kx - 1], wxp = gxr[kx], wym = gyr[ky - 1], wyp = gyr[ky];
-                V sxv, syv;
-                if (interior) {
-                    sxv = slope2i(ph[-VB], f0, ph[VB], wxm, wxp);
-                    syv = slope2i(ph[-PX * VB], f0, ph[PX * VB], wym, wyp);
-                } else {
-                    sxv = slope2(ph[-VB], f0, ph[VB], wxm, wxp, i > 0, i < nx - 1, nx > 1);
-                    syv = slope2(ph[-PX * VB], f0, ph[PX * VB], wym, wyp, j > 0, j < ny - 1, ny > 1);
-                }
-                if (dox) {
-                    const V d0 = pfma(sxv, bc(xneg ? -gxh[kx] : gxh[kx]), f0);
-                    F[slx * VB] = flux2(fpn + slx * NP, qoff, loff, exx, eyx, href, u, v, ub, vbb, d0, sxv, syv);
-                }
-                if (doy) {
-                    const V d0 = pfma(syv, bc(yneg ? -gyh[ky] : gyh[ky]), f0);
-                    F[sly * VB] = flux2(fpn + sly * NP, qoffy, loffy, exy, eyy, href, u, v, vbb, ub, d0, syv, sxv);
-                }
-            }
-        }
-        if (s > 0) {
-            // ---- pass 2, level s - 1: Eq. fv_h with the spectral source (delta form)
-            const int n = s - 1;
-            const V* F = fbuf + (size_t)(n & 1) * L::FLUX + lane;
-            V* on = cd.f[p ^ 1] + ((size_t)vb * nt + n) * nc * VB + lane;
-            const T* cpn = cps + (size_t)(n & 1) * L::CP;
-            const T* ctn = ctab + n * 2 * nuv;
-            constexpr int lvo = NCT * VB;                     // level stride of the own-cell store (pairs)
-#pragma unroll
-            for (int r = 0; r < (NCT + NW - 1) / NW; ++r) {
-                const int ct = warp + r * NW;
-                if (ct >= NCT) break;
-                const int ti = ct % TX, tj = ct / TX;
-                const int i = i0 + ti, j = j0 + tj;
-                if (i >= nx || j >= ny) continue;
-                const int c = j * nx + i;
-                const T* tb = ctn + c * nt * 2 * nuv;
-                const T ex0 = __ldg(tb + iu), ey0 = __ldg(tb + ivn);
-                const T ex1 = __ldg(tb + nuv + iu), ey1 = __ldg(tb + nuv + ivn);
-                const int fL = tj * (TX + 1) + ti, fB = NFX + tj * TX + ti;
-                const V dX = psub(F[(fL + 1) * VB], F[fL * VB]);
-                const V dY = psub(F[(fB + TX) * VB], F[fB * VB]);
-                V* fc = own + ct * VB + lane;                // level m at fc[m * lvo]
-                V e;
-                switch (implicit ? 0 : nh) {
-                    case 0: e = etb[0]; break;
-                    case 1: e = spectral2<1>(fc, n, nt, lvo, etb); break;
-                    case 2: e = spectral2<2>(fc, n, nt, lvo, etb); break;
-                    case 3: e = spectral2<3>(fc, n, nt, lvo, etb); break;
-                    case 4: e = spectral2<4>(fc, n, nt, lvo, etb); break;
-                    case 5: e = spectral2<5>(fc, n, nt, lvo, etb); break;
-                    case 6: e = spectral2<6>(fc, n, nt, lvo, etb); break;
-                    default: e = spectral2<7>(fc, n, nt, lvo, etb); break;
-                }
-                // equilibria of W^{k+1} (slot 1) and W^k (slot 0), delta form
-                const T* cp = cpn + ct * NCP;
-                const V q1 = eq2(cp + C_EQ1, ex1, ey1, href, u, v, r2, shakhov);
-                const V q0 = eq2(cp + C_EQ0, ex0, ey0, href, u, v, r2, shakhov);
-                const V* k = reinterpret_cast<const V*>(cp + C_K);   // kself, -kE, kp1, kp0, -kdx, -kdy
-                const V f0 = fc[n * lvo];
-                V x = pmul(k[0], f0);
-                x = pfma(k[4], dX, x);
-                x = pfma(k[5], dY, x);
-                x = pfma(k[1], e, x);
-                x = pfma(k[2], q1, x);
-                x = pfma(k[3], q0, x);
-                if (implicit) fc[n * lvo] = x;               // right-hand side of level n; h^k no longer needed
-                else on[c * VB] = x;
-            }
-        }
-        __syncthreads();
     }
     if (implicit) {
-        // spectral source at the new iterate: f^{k+1} = minv (right-hand sides over the levels), per cell and lane
-        constexpr int lvo = NCT * VB;
+        // spectral source at the new iterate: f^{k+1} = minv (right-hand sides over the levels), per cell, block
+        // and lane
         for (int ct = warp; ct < NCT; ct += NW) {
             const int ti = ct % TX, tj = ct / TX;
             const int i = i0 + ti, j = j0 + tj;
             if (i >= nx || j >= ny) continue;
             const int c = j * nx + i;
-            const V* fc = own + ct * VB + lane;
-            V rr[MAXNT];
-#pragma unroll
-            for (int m = 0; m < MAXNT; ++m) rr[m] = m < nt ? fc[m * lvo] : bc(T(0));
             const T* Mi = cd.minv + (size_t)c * nt * nt;
-            V* o = cd.f[p ^ 1] + (size_t)vb * nt * nc * VB + (size_t)c * VB + lane;
 #pragma unroll
-            for (int n = 0; n < MAXNT; ++n) {
-                if (n >= nt) break;
-                V acc = bc(T(0));
+            for (int h = 0; h < VPL; ++h) {
+                const V* fc = own + (size_t)(h * NCT + ct) * VB + lane;
+                V rr[MAXNT];
 #pragma unroll
-                for (int m = 0; m < MAXNT; ++m)
-                    if (m < nt) acc = pfma(bc(__ldg(Mi + n * nt + m)), rr[m], acc);
-                o[(size_t)n * nc * VB] = acc;
+                for (int m = 0; m < MAXNT; ++m) rr[m] = m < nt ? fc[m * LVO] : bc(T(0));
+                V* o = cd.f[p ^ 1] + (vb + h) * bstride + (size_t)c * VB + lane;
+#pragma unroll
+                for (int n = 0; n < MAXNT; ++n) {
+                    if (n >= nt) break;
+                    V acc = bc(T(0));
+#pragma unroll
+                    for (int m = 0; m < MAXNT; ++m)
+                        if (m < nt) acc = pfma(bc(__ldg(Mi + n * nt + m)), rr[m], acc);
+                    o[(size_t)n * nc * VB] = acc;
+                }
             }
         }
     }
 }
 
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, int VPL>
 constexpr size_t k4_cells_smem(int nt)
 {
-    return K4Layout<T, TX, TY>::bytes(nt);
+    return K4Layout<T, TX, TY, VPL>::bytes(nt);
 }
 
 }  // namespace hb

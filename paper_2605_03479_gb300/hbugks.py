@@ -62,7 +62,8 @@ EXPORTED = ("hbugks_workspace_bytes", "hbugks_create", "hbugks_destroy", "hbugks
             "hbugks_status_string", "hbugks_enqueue_iterations", "hbugks_profile_kernels",
             "hbugks_harmonic_noalloc", "hbugks_launches_per_iteration", "hbugks_get_tile_shape",
             "hbugks_set_tile_shape", "hbugks_cuda_error_string", "hbugks_test_expire_wait",
-            "hbugks_copy_state", "hbugks_set_loop_mode")
+            "hbugks_copy_state", "hbugks_set_loop_mode", "hbugks_get_micro_variant",
+            "hbugks_set_micro_variant")
 
 
 def lib():
@@ -102,6 +103,8 @@ def lib():
             L.hbugks_cuda_error_string.restype = C.c_char_p
             L.hbugks_get_tile_shape.argtypes = [vp, i, C.POINTER(i), C.POINTER(i)]
             L.hbugks_set_tile_shape.argtypes = [vp, i, i, i]
+            L.hbugks_get_micro_variant.argtypes = [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(i)]
+            L.hbugks_set_micro_variant.argtypes = [vp, i, i, i, i]
             L.hbugks_test_expire_wait.argtypes = [vp]
             L.hbugks_copy_state.argtypes = [vp, i, vp, i]
             L.hbugks_set_loop_mode.argtypes = [vp, i]
@@ -289,8 +292,19 @@ class Solver:
         return tx.value, ty.value
 
     def set_tile_shape(self, case_index: int, tx: int, ty: int) -> None:
-        """Pin the micro-update tile of a case (4x4, 4x2, 2x2 or 8x4)."""
+        """Pin the micro-update tile of a case (4x4, 4x2, 2x2 or 8x4, one velocity block per CTA)."""
         _check(lib().hbugks_set_tile_shape(self.h, case_index, tx, ty), "set_tile_shape")
+
+    def micro_variant(self, case_index: int = 0) -> tuple[int, int, int]:
+        """Micro-update variant of a case: tile (tx, ty) and velocity blocks per CTA."""
+        tx, ty, vpl = C.c_int(0), C.c_int(0), C.c_int(0)
+        _check(lib().hbugks_get_micro_variant(self.h, case_index, C.byref(tx), C.byref(ty), C.byref(vpl)),
+               "get_micro_variant")
+        return tx.value, ty.value, vpl.value
+
+    def set_micro_variant(self, case_index: int, tx: int, ty: int, vpl: int) -> None:
+        """Pin the micro-update variant of a case (a tile with 1 velocity block per CTA, or 4x2 with 2)."""
+        _check(lib().hbugks_set_micro_variant(self.h, case_index, tx, ty, vpl), "set_micro_variant")
 
     # ------------------------------------------------------------------ fields
     def level_fields(self, case_index: int, level: int):

@@ -238,7 +238,8 @@ def test_implicit_spectral_matches_oracle(hb, name, factory, niter, precision):
 # The configuration of the large thermal benchmark (64 x 64 midpoint velocities on [-4, 4], N_H = 5, Kn 0.05,
 # St 5, Pr 2/3, bottom wall T0 (1 + 0.5 sin wt)) on a 16 x 16 mesh: four interior tiles of 4 x 4 cells (the
 # paired first pass), wall and corner tiles, every spectral offset d = 1..5, from a seeded state.  Each precision
-# runs with two pinned micro-update tiles (FP64 needs the smaller tiles at N_T = 11 for shared memory).
+# runs with pinned micro-update variants (FP64 needs the smaller tiles at N_T = 11 for shared memory; FP32-split
+# also runs the two-block 4 x 2 variant that the autotuner picks for the 128 x 128 benchmark).
 _ORACLE_CACHE = {}
 
 
@@ -256,15 +257,17 @@ def _oracle_run(key, case, niter, seed):
     return _ORACLE_CACHE[key]
 
 
-@pytest.mark.parametrize("precision,tile", [(0, (4, 2)), (0, (2, 2)), (1, (4, 4)), (1, (8, 4))],
-                         ids=["fp64_tile4x2", "fp64_tile2x2", "fp32split_tile4x4", "fp32split_tile8x4"])
-def test_bench_grid_nh5_matches_oracle(hb, precision, tile):
+@pytest.mark.parametrize("precision,variant", [(0, (4, 2, 1)), (0, (2, 2, 1)), (1, (4, 4, 1)), (1, (8, 4, 1)),
+                                               (1, (4, 2, 2))],
+                         ids=["fp64_tile4x2", "fp64_tile2x2", "fp32split_tile4x4", "fp32split_tile8x4",
+                              "fp32split_tile4x2_two_blocks"])
+def test_bench_grid_nh5_matches_oracle(hb, precision, variant):
     case = _bench_grid_case()
     init, o, res_o = _oracle_run("bench_grid16", case, 2, seed=7)
     case.precision = precision
     s = hb.Solver(case)
-    s.set_tile_shape(0, *tile)
-    assert s.tile_shape(0) == tile
+    s.set_micro_variant(0, *variant)
+    assert s.micro_variant(0) == variant
     s.set_state(0, *init)
     rc, its, res_g = s.iterate(2)
     g = s.get_state(0)
