@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "HB-UGKS cell*velocity*level updates/s"
 # ncu DRAM bytes (read + write) per update of one k4_cells launch on the 64x64-cell, 64x64-velocity, N_T = 11
 # thermal cavity, by micro-update variant (tile x, tile y, velocity blocks per CTA); see profiles/
-K4_TRAFFIC_64 = {}
+K4_TRAFFIC_64 = {(4, 2, 2): 19.2881}
 UNIT = "updates/s"
 
 
