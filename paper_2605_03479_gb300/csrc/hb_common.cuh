@@ -409,17 +409,25 @@ struct PolyT {
     }
 };
 
+// C = u A (dir 0) or v A (dir 1), truncated at total degree 4: every product in the face parameters has a
+// monomial u_n or u_t as one factor, so it shifts the coefficients by one power
 template <typename P>
-__device__ __noinline__ void poly_mul(const PolyT<P>& A, const PolyT<P>& B, PolyT<P>& C)
+__device__ __forceinline__ void poly_shift(int dir, const PolyT<P>& A, PolyT<P>& C)
 {
     C.zero();
-    for (int p = 0; p < 5; ++p)
-        for (int q = 0; q < 5 - p; ++q) {
-            const P a = A.c[p][q];
-            if (a == P(0)) continue;
-            for (int r = 0; r < 5 - p; ++r)
-                for (int s = 0; s < 5 - p - q - r; ++s) C.c[p + r][q + s] += a * B.c[r][s];
-        }
+    if (dir == 0) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4 - p; ++q)
+                if (A.c[p][q] != P(0)) C.c[p + 1][q] = A.c[p][q];
+    } else {
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4 - p; ++q)
+                if (A.c[p][q] != P(0)) C.c[p][q + 1] = A.c[p][q];
+    }
 }
 
 // P_h(a) = a0 + a1 u + a2 v + a3/2 (u^2 + v^2 + 1/(2 lam)),  P_b(a) = P_h(a) + a3/(2 lam)
@@ -435,22 +443,35 @@ __device__ inline void poly_P(const double* a, double i2l, bool for_b, PolyT<P>&
 }
 
 // moments sum w psi [Q H ; R B] over the grid part selected by (rx, ry), H = pref e^{..}, B = H i2l:
-//   (sum Q H, sum u Q H, sum v Q H, 1/2 sum (|u|^2 Q H + R B))
+//   (sum Q H, sum u Q H, sum v Q H, 1/2 sum (|u|^2 Q H + R B)).  The selected rows of the 1-D sums are copied
+// through constant indices first, so that everything stays in registers.
 template <typename P>
-__device__ __noinline__ void mom4(const PolyT<P>& Q, const PolyT<P>& R, const SumsT<P>& X, int rx, const SumsT<P>& Y,
-                                  int ry, P pref, P i2l, P out[4])
+__device__ __forceinline__ void sum_row(const SumsT<P>& X, int r, P (&o)[9])
 {
+#pragma unroll
+    for (int q = 0; q < 9; ++q) o[q] = r == 0 ? X.s[0][q] : r == 1 ? X.s[1][q] : r == 2 ? X.s[2][q] : X.s[3][q];
+}
+
+template <typename P>
+__device__ __forceinline__ void mom4(const PolyT<P>& Q, const PolyT<P>& R, const SumsT<P>& X, int rx, const SumsT<P>& Y,
+                                     int ry, P pref, P i2l, P out[4])
+{
+    P xr[9], yr[9];
+    sum_row(X, rx, xr);
+    sum_row(Y, ry, yr);
     P o0 = 0, o1 = 0, o2 = 0, o3 = 0, ob = 0;
+#pragma unroll
     for (int p = 0; p < 5; ++p)
+#pragma unroll
         for (int q = 0; q < 5 - p; ++q) {
             const P a = Q.c[p][q], r = R.c[p][q];
             if (a != P(0)) {
-                o0 += a * X.s[rx][p] * Y.s[ry][q];
-                o1 += a * X.s[rx][p + 1] * Y.s[ry][q];
-                o2 += a * X.s[rx][p] * Y.s[ry][q + 1];
-                o3 += a * (X.s[rx][p + 2] * Y.s[ry][q] + X.s[rx][p] * Y.s[ry][q + 2]);
+                o0 += a * xr[p] * yr[q];
+                o1 += a * xr[p + 1] * yr[q];
+                o2 += a * xr[p] * yr[q + 1];
+                o3 += a * (xr[p + 2] * yr[q] + xr[p] * yr[q + 2]);
             }
-            if (r != P(0)) ob += r * X.s[rx][p] * Y.s[ry][q];
+            if (r != P(0)) ob += r * xr[p] * yr[q];
         }
     out[0] = pref * o0;
     out[1] = pref * o1;

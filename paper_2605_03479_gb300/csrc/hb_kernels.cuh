@@ -199,24 +199,41 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
     {
         const T dl = T(cd.lam0 - lamf);
         T tl = T(2.0 * lamf * U0), l2 = T(lamf * U0 * U0);
+        // the sums of the three node classes (positive, negative, zero) in registers: a node adds its term to
+        // its own class and zero to the other two
+        T sp_[9], sn_[9], sz_[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) { sp_[q] = T(0); sn_[q] = T(0); sz_[q] = T(0); }
         for (int k = 0; k < nu; ++k) {
             const T x = cd.tu1[k];
             const T e = t_expm1<T>(dl * x * x + tl * x - l2);
             tb[k] = e;
-            const int row = x > T(0) ? 1 : (x < T(0) ? 2 : 3);
+            const T ep = x > T(0) ? e : T(0), en = x < T(0) ? e : T(0), ez = x == T(0) ? e : T(0);
 #pragma unroll
-            for (int q = 0; q < 9; ++q) dX.s[row][q] += cd.wxr[q * nu + k] * e;
+            for (int q = 0; q < 9; ++q) {
+                const T wq = cd.wxr[q * nu + k];
+                sp_[q] += wq * ep; sn_[q] += wq * en; sz_[q] += wq * ez;
+            }
         }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) { dX.s[1][q] = sp_[q]; dX.s[2][q] = sn_[q]; dX.s[3][q] = sz_[q]; }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) { sp_[q] = T(0); sn_[q] = T(0); sz_[q] = T(0); }
         tl = T(2.0 * lamf * V0);
         l2 = T(lamf * V0 * V0);
         for (int k = 0; k < nv; ++k) {
             const T y = cd.tv1[k];
             const T e = t_expm1<T>(dl * y * y + tl * y - l2);
             tb[nu + k] = e;
-            const int row = y > T(0) ? 1 : (y < T(0) ? 2 : 3);
+            const T ep = y > T(0) ? e : T(0), en = y < T(0) ? e : T(0), ez = y == T(0) ? e : T(0);
 #pragma unroll
-            for (int q = 0; q < 9; ++q) dY.s[row][q] += cd.wyr[q * nv + k] * e;
+            for (int q = 0; q < 9; ++q) {
+                const T wq = cd.wyr[q * nv + k];
+                sp_[q] += wq * ep; sn_[q] += wq * en; sz_[q] += wq * ez;
+            }
         }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) { dY.s[1][q] = sp_[q]; dY.s[2][q] = sn_[q]; dY.s[3][q] = sz_[q]; }
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             dX.s[0][q] = dX.s[1][q] + dX.s[2][q] + dX.s[3][q];
@@ -234,19 +251,18 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
         }
     const T pref = T(rho0 * lamf / M_PI), i2l = T(0.5 / lamf);
     auto rows = [&](int r, int& rx, int& ry) { rx = ax == 0 ? r : 0; ry = ax == 0 ? 0 : r; };
-    PolyT<T> un, ut;
-    un.zero(); ut.zero();
-    if (ax == 0) { un.c[1][0] = T(1); ut.c[0][1] = T(1); } else { un.c[0][1] = T(1); ut.c[1][0] = T(1); }
+    // u_n and u_t as the axis a product by them shifts a polynomial along (0: u, 1: v)
+    const int axn = ax, axt = 1 - ax;
     PolyT<T> PhL, PbL, PhR, PbR, Pht, Pbt, t1, t2;
     poly_P<T>(aL, 0.5 / lamf, false, PhL); poly_P<T>(aL, 0.5 / lamf, true, PbL);
     poly_P<T>(aR, 0.5 / lamf, false, PhR); poly_P<T>(aR, 0.5 / lamf, true, PbR);
     poly_P<T>(at, 0.5 / lamf, false, Pht); poly_P<T>(at, 0.5 / lamf, true, Pbt);
     // Q_side = u_n P_h(a_side) + u_t P_h(a_t),  R_side likewise with P_b
     PolyT<T> QL, RL, QR, RR, Q0, R0;
-    poly_mul(un, PhL, QL); poly_mul(ut, Pht, t1);
-    poly_mul(un, PbL, RL); poly_mul(ut, Pbt, t2);
-    poly_mul(un, PhR, QR);
-    poly_mul(un, PbR, RR);
+    poly_shift(axn, PhL, QL); poly_shift(axt, Pht, t1);
+    poly_shift(axn, PbL, RL); poly_shift(axt, Pbt, t2);
+    poly_shift(axn, PhR, QR);
+    poly_shift(axn, PbR, RR);
 #pragma unroll
     for (int a = 0; a < 5; ++a)
 #pragma unroll
@@ -290,27 +306,27 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
     sb.c[0][0] += cq2.c[0][0]; sb.c[1][0] += cq2.c[1][0]; sb.c[0][1] += cq2.c[0][1];
     const int half = wall ? inc_row : 0;  // velocities carried by the integral solution
     PolyT<T> q1, r1;
-    poly_mul(un, shk, q1); poly_mul(un, sb, r1);
+    poly_shift(axn, shk, q1); poly_shift(axn, sb, r1);
     T F1s[4], F2[4], F3[4];
     rows(half, rx, ry);
     mom4(q1, r1, X, rx, Y, ry, pref, i2l, F1s);
     // C2 term: u_n (u_n P(a_bar) + u_t P(a_t)) with a_bar = a^L for u_n > 0, a^R for u_n < 0
     PolyT<T> uQ, uR;
     if (!wall) {
-        poly_mul(un, QL, uQ); poly_mul(un, RL, uR);
+        poly_shift(axn, QL, uQ); poly_shift(axn, RL, uR);
         rows(1, rx, ry); mom4(uQ, uR, X, rx, Y, ry, pref, i2l, F2);
-        poly_mul(un, QR, uQ); poly_mul(un, RR, uR);
+        poly_shift(axn, QR, uQ); poly_shift(axn, RR, uR);
         rows(2, rx, ry); mom4(uQ, uR, X, rx, Y, ry, pref, i2l, tmp);
 #pragma unroll
         for (int k = 0; k < 4; ++k) F2[k] += tmp[k];
     } else {
-        poly_mul(un, QL, uQ); poly_mul(un, RL, uR);
+        poly_shift(axn, QL, uQ); poly_shift(axn, RL, uR);
         rows(inc_row, rx, ry); mom4(uQ, uR, X, rx, Y, ry, pref, i2l, F2);
     }
     // C3 term: u_n P(A)
     PolyT<T> PhA, PbA;
     poly_P<T>(Aa, 0.5 / lamf, false, PhA); poly_P<T>(Aa, 0.5 / lamf, true, PbA);
-    poly_mul(un, PhA, uQ); poly_mul(un, PbA, uR);
+    poly_shift(axn, PhA, uQ); poly_shift(axn, PbA, uR);
     rows(half, rx, ry);
     mom4(uQ, uR, X, rx, Y, ry, pref, i2l, F3);
     // C1 term, Maxwellian part: moments of u_n psi (H0 - H_ref, B0 - B_ref), in FP64 from the reference sums

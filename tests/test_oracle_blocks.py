@@ -236,6 +236,58 @@ def test_local_step_closed_form():
             assert dG[j * c.nx + i] == pytest.approx(0.8 / (nu + 3.0 * 2), rel=1e-14)
 
 
+def _uniform_W(case, rho=1.0, U=0.0, V=0.0, T=1.0):
+    """Conservative variables of a uniform state on every level (D + K = 3 degrees of freedom, R T0 = 1/2)."""
+    W = np.zeros((case.nt, case.nc, 4))
+    W[..., 0] = rho
+    W[..., 1] = rho * U
+    W[..., 2] = rho * V
+    W[..., 3] = 0.5 * rho * (U * U + V * V) + 0.75 * rho * T
+    return W
+
+
+@pytest.mark.parametrize("nh", [1, 2, 5])
+def test_local_step_spectral_term_is_the_spectral_radius_of_omega_E(nh):
+    """Eq. dt_hb names omega N_H the spectral radius of the temporal differentiation matrix.  Between two
+    Strouhal numbers on the same state and mesh the convective term cancels: CFL (1/dG_2 - 1/dG_1) must equal
+    the difference of the largest |eigenvalue| of omega E, computed by numpy from the oracle's E."""
+    c1 = I.make_case("s1", 5, 8, kn=0.1, st=0.7, nh=nh, stretched_ratio=1.1)
+    c2 = I.make_case("s2", 5, 8, kn=0.1, st=6.0, nh=nh, stretched_ratio=1.1)
+    W = I.initial_state(c1, seed=4)[0]
+    d1 = O.cell_steps(O.Problem(c1), W)
+    d2 = O.cell_steps(O.Problem(c2), W)
+    E = O.E_matrix(c1.nt)
+    rad = lambda st: float(np.max(np.abs(np.linalg.eigvals(O.omega_from_st(st) * E))))
+    np.testing.assert_allclose(c1.cfl / d2 - c1.cfl / d1, rad(6.0) - rad(0.7), rtol=1e-11)
+    assert rad(1.0) == pytest.approx(nh, rel=1e-12)
+
+
+def test_local_step_convective_term_follows_cell_size_and_signal_speed():
+    """Eq. nu_conv on a uniform square mesh, uniform states: halving the cells doubles the convective rate;
+    widening the velocity space by dL adds dL (1/dx + 1/dy); a flow along x faster than the velocity-space bound
+    replaces the bound on x only; four times the temperature doubles the sound-speed part; the hottest level
+    sets the step of every level.  The spectral term is removed with a vanishing Strouhal number."""
+    st = 1e-12
+
+    def nu(case, W):
+        return case.cfl / O.cell_steps(O.Problem(case), W) - O.omega_from_st(st) * case.n_harmonics
+
+    c4 = I.make_case("m4", 4, 8, kn=0.1, st=st, nh=1)
+    c8 = I.make_case("m8", 8, 8, kn=0.1, st=st, nh=1)
+    n4 = nu(c4, _uniform_W(c4))
+    n8 = nu(c8, _uniform_W(c8))
+    np.testing.assert_allclose(n8, 2.0 * n4[0], rtol=1e-13)
+    inv = 4.0 + 4.0                                           # 1/dx + 1/dy on the 4 x 4 unit square
+    wide = I.make_case("w", 4, 8, kn=0.1, st=st, nh=1, half_width=6.0)
+    np.testing.assert_allclose(nu(wide, _uniform_W(wide)) - n4, 2.0 * inv, rtol=1e-13)
+    np.testing.assert_allclose(nu(c4, _uniform_W(c4, U=9.0)) - n4, (9.0 - 4.0) * 4.0, rtol=1e-13)
+    cs = math.sqrt((5.0 / 3.0) * 0.5)                         # sqrt(gamma R T0), gamma = 5/3, R T0 = 1/2
+    np.testing.assert_allclose(nu(c4, _uniform_W(c4, T=4.0)) - n4, cs * inv, rtol=1e-12)
+    Wmix = _uniform_W(c4)
+    Wmix[1] = _uniform_W(c4, T=4.0)[1]                        # one hot level
+    np.testing.assert_allclose(nu(c4, Wmix), nu(c4, _uniform_W(c4, T=4.0)), rtol=1e-14)
+
+
 def test_kn_and_st_maps_match_hand_values():
     rows = np.loadtxt(os.path.join(GOLD, "kn_map.txt"))
     for kn, mu0 in rows:
