@@ -281,6 +281,10 @@ template <typename T>
 void layout_case(Carver& cv, const HostCase& h, CaseDev<T>& d)
 {
     d.nx = h.nx; d.ny = h.ny; d.nu = h.nu; d.nv = h.nv; d.nvel = h.nvel; d.nvb = h.nvb;
+    for (int c = 0, e = 0; c < 4; ++c) {
+        for (int cl : h.vcls) e += cl == c;
+        d.cls_end[c] = e;
+    }
     d.nt = h.nt; d.nh = h.nh; d.nfx = h.nfx; d.nf = h.nf; d.nc = h.nc;
     d.face_step = h.src.phys.face_step;
     d.omega = h.omega; d.mu0 = h.mu0; d.w_vss = h.src.phys.w_vss; d.pr = h.src.phys.pr;

@@ -218,7 +218,6 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
     const T* __restrict__ tu = cd.tu;
     const T* __restrict__ tv = cd.tv;
     const T* __restrict__ tw = SEP ? cd.twv : cd.tw;       // SEP: the v-factor w_v of each weight
-    const int* __restrict__ vcls = cd.vcls;
 
     // general: the 23 + 23 + 13 sums per lane; SEP: v-moments per lane (x-face h: 4, b: 2, tangential h: 3,
     // b: 1, normal-flux h: 3, b: 1; the y-face alike; cell h: 4, b: 2), folded into the 23 + 23 + 13 at a
@@ -246,7 +245,7 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
     zero_cell();
 #pragma unroll
     for (int q = 0; q < NCM; ++q) ac[q] = T(0);
-    int cur = -1;
+    int cur = -1, cend = 0;                                  // current sign class, the first block past it
     T ul = T(0), wul = T(0);                                 // SEP: the lane's u and w_u in the current class
     // the 14 v-moments of a face (SEP) or its 23 sums (general) in slot order
     auto face_sums = [&](const V (&P)[NXP], const T (&S_)[NXS], T (&m)[SEP ? 14 : NM]) {
@@ -325,30 +324,34 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
         }
         const V* cb = buf + (size_t)(k % S) * G * blk;
         const int vb0 = k * G, gk = min(G, nvb - vb0);
-        if (valid) {
+        // the blocks of the chunk; INNER: every neighbour of the warp's cell exists (no wall branches)
+        auto run_blocks = [&](auto inner_tag) {
+            constexpr bool INNER = decltype(inner_tag)::value;
             // the velocities of block g + 1 are loaded while block g is summed
-            int ncls = __ldg(vcls + vb0);
             T nu_ = __ldg(tu + vb0 * VB + lane), nv_ = __ldg(tv + vb0 * VB + lane), nw_ = __ldg(tw + vb0 * VB + lane);
             for (int g = 0; g < gk; ++g) {
-                const int cls = ncls;
                 const T u = nu_, v = nv_, w = nw_;
                 if (g + 1 < gk) {
                     const int a1 = (vb0 + g + 1) * VB + lane;
-                    ncls = __ldg(vcls + vb0 + g + 1);
                     nu_ = __ldg(tu + a1); nv_ = __ldg(tv + a1); nw_ = __ldg(tw + a1);
                 }
-                if (cls != cur) {
+                // the classes occupy consecutive blocks: a new one starts where the current one ends
+                if (vb0 + g >= cend) {
                     if (cur >= 0) flush();
-                    cur = cls;
+                    do {
+                        ++cur;
+                        cend = cd.cls_end[cur];
+                    } while (vb0 + g >= cend);
                     if (SEP) {
                         ul = u;
                         wul = __ldg(cd.twu + (vb0 + g) * VB + lane);
                     }
                 }
+                const int cls = cur;
                 const V* ph = cb + (size_t)g * blk + (size_t)kc * VB + lane;
                 const V f0 = ph[0];
                 V sxv, syv;
-                if (inner) {
+                if constexpr (INNER) {
                     sxv = slope2i(ph[-VB], f0, ph[VB], wxm, wxp);
                     syv = slope2i(ph[-PX * VB], f0, ph[PX * VB], wym, wyp);
                 } else {
@@ -358,7 +361,7 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
                 const bool xn = (cls & 1) != 0, yn = (cls & 2) != 0;
                 V dx = pfma(sxv, bc(xn ? -hxh : hxh), f0);       // reconstruction at the downwind x-face
                 V dy = pfma(syv, bc(yn ? -hyh : hyh), f0);
-                if (!inner) {
+                if constexpr (!INNER) {
                     // a velocity parallel to a wall carries nothing into it
                     if ((xn ? !hm : !hp) && u == T(0)) dx = bc(T(0));
                     if ((yn ? !vm : !vp) && v == T(0)) dy = bc(T(0));
@@ -406,6 +409,10 @@ __global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
                     yp[4] = pfma(ty, bc(w), yp[4]); ys[10] += ty.x * wu; ys[11] += ty.x * wv; ys[12] += ty.x * wq;
                 }
             }
+        };
+        if (valid) {
+            if (inner) run_blocks(std::true_type{});
+            else run_blocks(std::false_type{});
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[k % S]);

@@ -10,6 +10,7 @@
 // balance because the signed face lengths of a rectangle sum to zero.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace hb {
@@ -127,6 +128,7 @@ struct CaseDev {
     const int* viv;                    // per stored velocity: v index
     const int* vcan;                   // per stored velocity: canonical index jv * nu + iu, -1 for padding
     const int* vcls;                   // per velocity block: sign class (bit 0: u < 0, bit 1: v < 0)
+    int cls_end[4];                    // one past the last block of sign classes 0..c (classes are consecutive)
     int shakhov;                       // Pr != 1
     double* fflux;                     // [nf][nt][4]
     T* cpar;                           // [nt][nc][NCP]
