@@ -274,7 +274,7 @@ void fill_host(HostCase& h, const hbugks_case& c)
     h.k2b = (h.nf * h.nt + 127) / 128;
     h.k3b = (h.nc + K3_THREADS - 1) / K3_THREADS;
     h.ksb = (h.nc + 127) / 128;
-    h.ktb = (h.nc * h.nt + 3) / 4;
+    h.ktb = (h.nc * h.nt + KT_ITEMS - 1) / KT_ITEMS;
 }
 
 template <typename T>
@@ -759,7 +759,7 @@ void enqueue_iteration(Impl<T>& im, int ncases, cudaStream_t s, cudaEvent_t* ev 
             case 0: launch_k1<T>(sp.shape, sp.total, sp.smem, b, s); break;
             case 1: k2_face_params<T><<<sp.total, 128, 0, s>>>(b); break;
             case 2: k3_macro<T><<<sp.total, K3_THREADS, 0, s>>>(b); break;
-            case 3: k_tables<T><<<sp.total, 128, 0, s>>>(b); break;
+            case 3: k_tables<T><<<sp.total, KT_ITEMS, 0, s>>>(b); break;
             case 4: launch_k4<T>(im.any_implicit, sp.shape, sp.total, sp.smem, b, s); break;
         }
     }

@@ -417,43 +417,54 @@ __global__ void __launch_bounds__(128) k2_face_params(Batch<T> B)
 // ------------------------------------------------------------------------------ separable Maxwellian tables
 
 // Tables of expm1(lam0 x^2 - lam (x - U)^2) over the 1-D velocity nodes, so that for a Maxwellian of density
-// rho: H - H_ref = H_ref [(r - 1) + r (ex + ey + ex ey)], r = rho lam / lam0.  One warp per face-level (interface
-// and, at walls, reflected Maxwellian) or cell-level (W^k and W^{k+1}); lanes over the nodes.
+// rho: H - H_ref = H_ref [(r - 1) + r (ex + ey + ex ey)], r = rho lam / lam0.  The cell-level tables of W^k and
+// W^{k+1}: a CTA takes 128 cell-levels; each thread first forms the exponent coefficients of one of them in
+// FP64 (one thread per cell-level, so the slow FP64 divisions run on every lane), then each warp writes the
+// tables of 32 of them with its lanes over the nodes.  (The interface and wall tables are formed in
+// k2_face_params.)
+constexpr int KT_ITEMS = 128;   // cell-levels per CTA of k_tables (one per thread)
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_tables(Batch<T> B)
+__global__ void __launch_bounds__(KT_ITEMS) k_tables(Batch<T> B)
 {
     const int cs = find_case(B.off, B.ncases, blockIdx.x);
     const CaseDev<T>& cd = B.cases[cs];
     if (!cd.st->active || *(volatile int*)cd.err) return;
-    const int lane = threadIdx.x & 31;
-    const int item = (blockIdx.x - B.off[cs]) * 4 + (threadIdx.x >> 5);   // cell-level pair, c * nt + n
-    const int nt = cd.nt, nuv = cd.nu + cd.nv;
-    if (item >= cd.nc * nt) return;
+    __shared__ T coef[KT_ITEMS][2][5];
+    const int nt = cd.nt, nuv = cd.nu + cd.nv, nitems = cd.nc * nt;
+    const int first = (blockIdx.x - B.off[cs]) * KT_ITEMS;   // cell-level pairs first.., item = c * nt + n
     const int p = cd.st->parity;
-    // lane e < 2 forms the exponent coefficients of W^k (e = 0) and W^{k+1} (e = 1) once (FP64 divisions are
-    // slow), the warp shares them
-    T q[5] = {T(0), T(0), T(0), T(0), T(0)};
-    if (lane < 2) {
-        double rho, U, V, lam;
-        prim((lane == 0 ? cd.W[p] : cd.W[p ^ 1]) + ((size_t)(item % nt) * cd.nc + item / nt) * 4, rho, U, V, lam);
-        q[0] = T(cd.lam0 - lam);
-        q[1] = T(2.0 * lam * U);
-        q[2] = T(lam * U * U);
-        q[3] = T(2.0 * lam * V);
-        q[4] = T(lam * V * V);
-    }
-    for (int e = 0; e < 2; ++e) {
-        T c[5];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) c[k] = __shfl_sync(0xffffffffu, q[k], e);
-        T* dst = cd.ctab + ((size_t)item * 2 + e) * nuv;
-        for (int k = lane; k < cd.nu; k += 32) {
-            const T x = cd.tu1[k];
-            dst[k] = t_expm1<T>(c[0] * x * x + c[1] * x - c[2]);
+    {
+        const int item = first + threadIdx.x;
+        if (item < nitems) {
+            for (int e = 0; e < 2; ++e) {
+                double rho, U, V, lam;
+                prim((e == 0 ? cd.W[p] : cd.W[p ^ 1]) + ((size_t)(item % nt) * cd.nc + item / nt) * 4, rho, U, V, lam);
+                T* q = coef[threadIdx.x][e];
+                q[0] = T(cd.lam0 - lam);
+                q[1] = T(2.0 * lam * U);
+                q[2] = T(lam * U * U);
+                q[3] = T(2.0 * lam * V);
+                q[4] = T(lam * V * V);
+            }
         }
-        for (int k = lane; k < cd.nv; k += 32) {
-            const T y = cd.tv1[k];
-            dst[cd.nu + k] = t_expm1<T>(c[0] * y * y + c[3] * y - c[4]);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = 0; r < 32; ++r) {
+        const int li = warp * 32 + r, item = first + li;
+        if (item >= nitems) break;
+        for (int e = 0; e < 2; ++e) {
+            const T* c = coef[li][e];
+            T* dst = cd.ctab + ((size_t)item * 2 + e) * nuv;
+            for (int k = lane; k < cd.nu; k += 32) {
+                const T x = cd.tu1[k];
+                dst[k] = t_expm1<T>(c[0] * x * x + c[1] * x - c[2]);
+            }
+            for (int k = lane; k < cd.nv; k += 32) {
+                const T y = cd.tv1[k];
+                dst[cd.nu + k] = t_expm1<T>(c[0] * y * y + c[3] * y - c[4]);
+            }
         }
     }
 }
