@@ -103,7 +103,7 @@ struct HostCase {
 
 // K1 tile (TX x TY cells, one warp each) and velocity blocks staged per pass, per storage precision
 template <typename T> constexpr int K1_TX = 4;
-template <typename T> constexpr int K1_TY = std::is_same<T, float>::value ? 4 : 2;
+template <typename T> constexpr int K1_TY = 2;
 template <typename T> constexpr int K1_G = std::is_same<T, float>::value ? 6 : 4;
 template <typename T> constexpr int K1_S = 3;   // pipeline stages of the staged velocity blocks
 

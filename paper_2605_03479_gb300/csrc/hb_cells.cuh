@@ -144,7 +144,7 @@ __device__ __forceinline__ T lane_totals(T (&v)[N], int lane)
 // w u^a v^b d factors into w_u u^a (the lane's) times sum over the lane's velocities of w_v v^b d, and the lane
 // keeps only those v-moments (34 sums instead of 59), multiplying by w_u u^a when the class changes.
 template <typename T, int TX, int TY, int G, int S, bool SEP>
-__global__ void __launch_bounds__(TX * TY * 32, 1) k1_cells(Batch<T> B)
+__global__ void __launch_bounds__(TX * TY * 32, (sizeof(T) == 4 && TX * TY == 8) ? 2 : 1) k1_cells(Batch<T> B)
 {
     using V = P2<T>;
     constexpr int PX = TX + 2, PY = TY + 2, NR = PX * PY, NWC = TX * TY;
