@@ -864,12 +864,13 @@ hbugks_status upload_offsets(hbugks_t h, Impl<T>& im)
     return HBUGKS_OK;
 }
 
-// ------------------------------------------------------------------------------ autotuner of the K4 tile
-// The micro update's tile (cells per CTA) trades halo re-reads and pass-1 work against shared memory per CTA
-// and so against CTAs per SM; which wins depends on the level count, the velocity grid, the mesh and the GPU.
-// Each feasible shape is timed on the case itself (one warm-up launch, then three), after one iteration from
-// rest has filled the parameters the kernel reads.  Choices are cached per process by everything that sets
-// the launch: mesh size, velocity grid, blocks, levels, precision and SM count.
+// ------------------------------------------------------------------------------ autotuner of the K4 variant
+// The micro update's variant (cells per CTA, velocity blocks per CTA) trades halo re-reads, pass-1 work and the
+// indices and parameters shared by a CTA's blocks against shared memory per CTA and so against CTAs per SM;
+// which wins depends on the level count, the velocity grid, the mesh and the GPU.  Each variant the case can
+// run is timed on the case itself (one warm-up launch, then three), after one iteration from rest has filled
+// the parameters the kernel reads.  Choices are cached per process by everything that sets the launch: mesh
+// size, velocity grid, blocks, levels, precision, SM count and the form of the spectral source.
 
 struct TuneCache {
     std::mutex mu;
